@@ -1,0 +1,398 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests re-types an oracle formula: each compares the oracle with
+an independent fact (a closed form the paper prints, an invariant, a library
+routine, brute-force quadrature, or a value printed in the paper).
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "paper_values.json")))
+
+
+def rand_sphere(rng, K):
+    x = rng.standard_normal(2 * K)
+    return x / np.linalg.norm(x)
+
+
+# --------------------------------------------------------------- random stream
+def test_philox_matches_triton_library():
+    """Philox4x32-10 against an independent implementation: Triton's
+    tl.philox run by its CPU interpreter (key = (seed_lo, seed_hi))."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(4, 16), dtype=np.uint64)
+    seeds = [0, 1, 0x0123456789ABCDEF & 0x7FFFFFFFFFFFFFFF, 2**40 + 17]
+    script = textwrap.dedent(
+        """
+        import os, sys, json
+        os.environ["TRITON_INTERPRET"] = "1"
+        import numpy as np, torch, triton, triton.language as tl
+        @triton.jit
+        def k(seed, c0p, c1p, c2p, c3p, o0, o1, o2, o3, N: tl.constexpr):
+            i = tl.arange(0, N)
+            c0 = tl.load(c0p + i); c1 = tl.load(c1p + i); c2 = tl.load(c2p + i); c3 = tl.load(c3p + i)
+            r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
+            tl.store(o0 + i, r0); tl.store(o1 + i, r1); tl.store(o2 + i, r2); tl.store(o3 + i, r3)
+        inp = json.load(sys.stdin)
+        out = {}
+        for s in inp["seeds"]:
+            c = [torch.tensor(np.array(v, dtype=np.uint32).view(np.int32)) for v in inp["ctr"]]
+            o = [torch.empty(len(inp["ctr"][0]), dtype=torch.int32) for _ in range(4)]
+            k[(1,)](s, *c, *o, N=len(inp["ctr"][0]))
+            out[str(s)] = [x.numpy().view(np.uint32).tolist() for x in o]
+        print(json.dumps(out))
+        """
+    )
+    res = subprocess.run([sys.executable, "-c", script], input=json.dumps(
+        {"seeds": seeds, "ctr": ctr.tolist()}), capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    ref = json.loads(res.stdout.strip().splitlines()[-1])
+    for s in seeds:
+        for i in range(ctr.shape[1]):
+            mine = O.philox([int(ctr[j, i]) for j in range(4)], [s & 0xFFFFFFFF, s >> 32])
+            theirs = [ref[str(s)][j][i] for j in range(4)]
+            assert mine == theirs, (s, i, mine, theirs)
+
+
+def test_uniform_map_properties():
+    ws = np.array([0, 1, 511, 512, 2**31, 2**32 - 512, 2**32 - 1], dtype=np.uint64)
+    for w in ws:
+        u = O.uniform(int(w))
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u  # exactly representable in FP32
+        assert abs(u + O.uniform(int(w) ^ 0xFFFFFFFF) - 1.0) == 0.0  # u(~w) = 1 - u(w)
+    assert O.uniform(0) == 2.0**-24 and O.uniform(2**32 - 1) == 1.0 - 2.0**-24
+
+
+def test_stream_normals_are_standard_normal():
+    sp = pytest.importorskip("scipy.stats")
+    K = 16
+    z = np.concatenate([O.stream(K, 99, 3, i)[0] for i in range(6000)])
+    assert sp.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 4 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 4 * math.sqrt(2 / z.size)
+    us = np.array([O.stream(K, 99, 3, i)[1] for i in range(6000)])
+    assert sp.kstest(us, "uniform").pvalue > 1e-3
+    # cos and sin halves of one pair are uncorrelated
+    zz = np.array([O.stream(K, 5, 0, i)[0] for i in range(6000)])
+    c = np.corrcoef(zz[:, 0], zz[:, K])[0, 1]
+    assert abs(c) < 4 / math.sqrt(6000)
+
+
+def test_stream_depends_on_every_counter_field():
+    K = 8
+    base = O.stream(K, 1, 0, 5)[0]
+    for args in [(2, 0, 5), (1, 1, 5), (1, 0, 6), (1, 0, 5 + (1 << 32))]:
+        assert not np.allclose(O.stream(K, *args)[0], base)
+
+
+# --------------------------------------------------------------- Hamiltonian
+def test_appendix_A_two_mode_exact():
+    """Appendix A: H2 = 2 pi (R1^2 + 4 R2^2), H3 = 2 pi R2 R1^2 cos(2 th1 - th2)."""
+    rng = np.random.default_rng(1)
+    for E0 in (1.0, 0.5, 2.0):
+        c = math.sqrt(E0 / (2 * math.pi))
+        for _ in range(50):
+            t1, t2, ph = rng.uniform(0, 2 * math.pi, 3)
+            R1, R2 = c * math.cos(ph), c * math.sin(ph)
+            u1, u2 = R1 * np.exp(1j * t1), R2 * np.exp(1j * t2)
+            xh = np.array([u1.real, u2.real, -u1.imag, -u2.imag]) / c
+            assert abs(O.H2(2, E0, xh) - 2 * math.pi * (R1**2 + 4 * R2**2)) < 1e-14
+            assert abs(O.H3_double(2, E0, xh) - 2 * math.pi * R2 * R1**2 * math.cos(2 * t1 - t2)) < 1e-14
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 8, 16, 32, 64])
+def test_H3_three_forms_agree(K):
+    """Double sum (Eq. 42) = triple sum (Eq. 41) = grid cubature of Eq. (2) with N > 3K."""
+    rng = np.random.default_rng(K)
+    for _ in range(5):
+        xh = rand_sphere(rng, K)
+        d = O.H3_double(K, 1.3, xh)
+        assert abs(O.H3_triple(K, 1.3, xh) - d) < 1e-13
+        assert abs(O.H3_grid(K, 1.3, xh, 3 * K + 1) - d) < 1e-13
+        assert abs(O.H3_grid(K, 1.3, xh, 4 * K) - d) < 1e-13
+
+
+def test_grid_needs_more_than_3K_points():
+    rng = np.random.default_rng(3)
+    K = 16
+    errs = [abs(O.H3_grid(K, 1.0, x, 3 * K) - O.H3_double(K, 1.0, x))
+            for x in (rand_sphere(rng, K) for _ in range(20))]
+    assert max(errs) > 1e-6
+
+
+def test_H3_structure():
+    rng = np.random.default_rng(4)
+    for K in (4, 16, 32):
+        for k in range(1, K + 1):  # a single active mode forms no triad
+            xh = np.zeros(2 * K)
+            ph = rng.uniform(0, 2 * math.pi)
+            xh[k - 1], xh[K + k - 1] = math.cos(ph), math.sin(ph)
+            assert abs(O.H3_double(K, 1.0, xh)) < 1e-15
+            assert abs(O.H2(K, 1.0, xh) - k * k) < 1e-12
+        xh = rand_sphere(rng, K)
+        assert abs(O.H3_double(K, 1.0, -xh) + O.H3_double(K, 1.0, xh)) < 1e-15  # odd
+        assert O.H2(K, 1.0, -xh) == O.H2(K, 1.0, xh)  # even
+        # translation xi -> xi + s rotates u_k by e^{iks}: H2, H3 invariant, u shifts
+        s = 0.37
+        uk = xh[:K] - 1j * xh[K:]
+        uk2 = uk * np.exp(1j * np.arange(1, K + 1) * s)
+        xs = np.concatenate([uk2.real, -uk2.imag])
+        assert abs(O.H3_double(K, 1.0, xs) - O.H3_double(K, 1.0, xh)) < 1e-14
+        assert abs(O.H2(K, 1.0, xs) - O.H2(K, 1.0, xh)) < 1e-12
+        assert abs(O.u_at(K, 1.0, xs, 0.2) - O.u_at(K, 1.0, xh, 0.2 + s)) < 1e-13
+
+
+def test_energy_constraint_after_projection():
+    """Eq. (12): (pi/2) sum (a_k^2 + b_k^2) = E0 for every projected proposal, and
+    E[u] = (1/2) int u^2 = E0 by the grid."""
+    for prop in (O.UNIFORM, O.PAPER):
+        pt = O.make_point(16, 1.7, 30.0, 50.0, prop, logM=0.0)
+        rec = O.replay(pt, 11, 0, np.arange(200, dtype=np.uint64), nthreads=2)
+        c2 = 2 * math.sqrt(1.7 / (2 * math.pi))
+        for xh in rec["xhat"]:
+            a, b = c2 * xh[:16], c2 * xh[16:]
+            assert abs(math.pi / 2 * np.sum(a * a + b * b) - 1.7) < 1e-13
+            N = 64
+            u = np.array([O.u_at(16, 1.7, xh, -math.pi + 2 * math.pi * j / N) for j in range(N)])
+            assert abs(0.5 * np.sum(u * u) * 2 * math.pi / N - 1.7) < 1e-12
+
+
+def test_dirichlet_kernel():
+    """Eq. (46): u_k = sqrt(E0/(2 pi K)); its peak u(0) is the largest displacement
+    any field of energy E0 reaches (Cauchy-Schwarz), and H3 = pi K (K-1) c^3."""
+    for K in (16, 32):
+        xh = np.zeros(2 * K)
+        xh[:K] = 1 / math.sqrt(K)
+        cp = math.sqrt(1.0 / (2 * math.pi * K))
+        assert abs(O.H3_double(K, 1.0, xh) - math.pi * K * (K - 1) * cp**3) < 1e-13
+        ucap = math.sqrt(2 * K / math.pi)
+        assert abs(O.u_at(K, 1.0, xh, 0.0) - ucap) < 1e-12
+        rng = np.random.default_rng(K)
+        for _ in range(200):
+            assert O.u_at(K, 1.0, rand_sphere(rng, K), rng.uniform(-3, 3)) <= ucap + 1e-12
+    # the paper prints u_max = 3.09 / 4.44 (Sec. V.D); the bound of Eq. (46) is
+    # sqrt(2 K E0 / pi) = 3.19 / 4.51, which the printed values undershoot.
+    assert math.sqrt(2 * 16 / math.pi) > GOLD["u_max_printed"]["K16"]
+    assert math.sqrt(2 * 32 / math.pi) > GOLD["u_max_printed"]["K32"]
+
+
+# ------------------------------------------------------------------ alpha*
+def test_alpha_star():
+    a = O.alpha_star(32, 20.0)
+    assert abs(a - GOLD["alpha_star_K32_bp20"]["value"]) < 0.05
+    assert abs(O.F_alpha(32, 20.0, a)) < 1e-14
+    assert O.alpha_star(16, 0.0) == pytest.approx(1.0, abs=1e-15)  # F = 1 - alpha
+    seq = [O.alpha_star(K, 20.0) for K in (8, 16, 32, 64, 128)]
+    assert all(x > y for x, y in zip(seq, seq[1:])) and seq[-1] > 1.0 and seq[-1] < 1.1
+    # K = 1: F = 1 - alpha/(1 + alpha beta') has the root 1/(1 - beta')
+    assert O.alpha_star(1, 0.5) == pytest.approx(2.0, rel=1e-14)
+    # no root once beta' >= K^2 sum 1/k^2
+    for K in (16, 32):
+        bound = K * K * sum(1.0 / k**2 for k in range(1, K + 1))
+        assert math.isnan(O.alpha_star(K, bound * 1.001))
+        assert not math.isnan(O.alpha_star(K, bound * 0.999))
+
+
+# ---------------------------------------------------------------- envelope M
+def logM_r0_paper(K, bp):
+    """r = 0: log f/g depends on xh only through S in [1, K^2];
+    h(S) = -beta' S/K^2 + K ln(1 + c S), c = alpha* beta'/K^3, is concave with
+    stationary point S* = (alpha* - 1)/c."""
+    a = O.alpha_star(K, bp)
+    c = a * bp / K**3
+    S = min(max((a - 1) / c, 1.0), K * K)
+    return -bp * S / K**2 + K * math.log1p(c * S)
+
+
+@pytest.mark.parametrize("K,bp", [(8, 30.0), (16, 20.0), (16, 60.0)])
+def test_logM_r0_closed_form(K, bp):
+    pt = O.make_point(K, 1.0, bp, 0.0, O.PAPER)
+    assert abs(O.log_M(pt, 0) - logM_r0_paper(K, bp)) < 1e-10
+    pu = O.make_point(K, 1.0, bp, 0.0, O.UNIFORM)
+    assert abs(O.log_M(pu, 0) - (-bp / K**2)) < 1e-10  # max of -beta' S/K^2 at S = 1
+
+
+def k2_reduced(E0, bp, r, prop):
+    """K = 2 in the coordinates of Appendix A: s_1 = cos^2 phi, s_2 = sin^2 phi,
+    H2 = 2 pi c^2 (cos^2 + 4 sin^2) (times E0/(2 pi c^2) = 1), and
+    H3 = 2 pi c^3 cos^2 phi sin phi cos psi, psi = 2 th1 - th2."""
+    c = math.sqrt(E0 / (2 * math.pi))
+    a = O.alpha_star(2, bp) if prop == O.PAPER else 1.0
+    w = [1 + a * bp * k * k / 8 if prop == O.PAPER else 1.0 for k in (1, 2)]
+
+    def ell(phi, psi):
+        s1, s2 = math.cos(phi) ** 2, math.sin(phi) ** 2
+        H2 = E0 * (s1 + 4 * s2)
+        H3 = 2 * math.pi * c**3 * s1 * math.sin(phi) * math.cos(psi)
+        v = -bp / (E0 * 4) * (H2 - r * H3)
+        if prop == O.PAPER:
+            v += 2 * math.log(w[0] * s1 + w[1] * s2)
+        return v
+
+    return ell, w, c
+
+
+@pytest.mark.parametrize("prop", [O.UNIFORM, O.PAPER])
+@pytest.mark.parametrize("bp,r", [(3.0, 40.0), (4.5, 10.0), (1.0, 0.0)])
+def test_K2_logM_and_acceptance_by_quadrature(prop, bp, r):
+    """K = 2: log M by brute-force maximisation over (phi, psi) and the acceptance
+    rate by quadrature of E_mu0[exp(-beta H)] (Bessel I0 in psi), against the
+    oracle's Nelder-Mead and a Monte-Carlo run of the whole oracle sampler."""
+    sp = pytest.importorskip("scipy")
+    from scipy import integrate, optimize, special
+    E0 = 1.0
+    ell, w, c = k2_reduced(E0, bp, r, prop)
+    phis = np.linspace(0, math.pi / 2, 4001)
+    vals = np.array([max(ell(p, 0.0), ell(p, math.pi)) for p in phis])
+    p0 = phis[int(np.argmax(vals))]
+    res = optimize.minimize_scalar(lambda p: -max(ell(p, 0.0), ell(p, math.pi)),
+                                   bounds=(max(p0 - 1e-3, 0), min(p0 + 1e-3, math.pi / 2)),
+                                   method="bounded", options={"xatol": 1e-12})
+    logM_bf = max(-res.fun, vals.max())
+    pt = O.make_point(2, E0, bp, r, prop)
+    logM = O.log_M(pt, 2)
+    assert abs(logM - logM_bf) < 1e-9
+
+    def integrand(phi):
+        s1, s2 = math.cos(phi) ** 2, math.sin(phi) ** 2
+        bh2 = bp / (E0 * 4) * E0 * (s1 + 4 * s2)
+        amp = bp / (E0 * 4) * r * 2 * math.pi * c**3 * s1 * math.sin(phi)
+        return math.sin(2 * phi) * math.exp(-bh2) * special.i0(amp)
+
+    Z = integrate.quad(integrand, 0, math.pi / 2, epsabs=1e-14, epsrel=1e-12)[0]
+    acc = Z * (w[0] * w[1] if prop == O.PAPER else 1.0) * math.exp(-logM_bf)
+    assert 0 < acc <= 1
+    pt.logM = logM
+    n = 1 << 19
+    st = O.run_stats(pt, 2024, 0, 0, n)
+    p = st["n_acc"] / n
+    se = math.sqrt(acc * (1 - acc) / n)
+    assert abs(p - acc) < 4 * se + 1e-12, (p, acc, se)
+    assert st["n_viol"] == 0 and st["max_delta"] <= 0
+
+
+def test_K1_accepts_everything():
+    for prop in (O.UNIFORM, O.PAPER):
+        pt = O.make_point(1, 1.0, 0.5, 100.0, prop)
+        pt.logM = O.log_M(pt, 1)
+        st = O.run_stats(pt, 1, 0, 0, 4096)
+        assert st["n_acc"] == 4096
+
+
+def test_beta_zero_is_uniform_measure():
+    """beta' = 0: the Gibbs measure is mu0 (Sec. II.C), both proposals accept
+    every draw, u0 has variance E0/pi and kurtosis 3K/(K+1) (a coordinate of a
+    uniform point on S^{2K-1}), and zero skewness."""
+    K, E0 = 16, 1.4
+    for prop in (O.UNIFORM, O.PAPER):
+        pt = O.make_point(K, E0, 0.0, 75.0, prop)
+        assert O.log_M(pt, 0) == pytest.approx(0.0, abs=1e-14)
+        pt.logM = 0.0
+        n = 1 << 18
+        st = O.run_stats(pt, 3, 1, 0, n)
+        assert st["n_acc"] == n
+        m = O.moments(n, st["sum_u0"])
+        assert abs(m["var"] - E0 / math.pi) < 4 * E0 / math.pi * math.sqrt(2 / n) * 1.2
+        assert abs(m["skew"]) < 4 * math.sqrt(6 / n)
+        assert abs(m["kurt"] - 3 * K / (K + 1)) < 4 * math.sqrt(24 / n)
+        # u0 / u_cap is one coordinate of a uniform point on S^{2K-1}: (y+1)/2 is
+        # Beta(K - 1/2, K - 1/2).  Histogram and exceedance counts follow it.
+        from scipy import stats as sps
+        ucap = math.sqrt(2 * K * E0 / math.pi)
+        beta = sps.beta(K - 0.5, K - 0.5)
+        edges = np.linspace(-ucap, ucap, 257)
+        probs = np.diff(beta.cdf((edges / ucap + 1) / 2))
+        hist = st["hist"].astype(float)
+        keep = probs * n > 20
+        chi2 = np.sum((hist[keep] - n * probs[keep]) ** 2 / (n * probs[keep]))
+        assert chi2 < keep.sum() + 6 * math.sqrt(2 * keep.sum())
+        sigma0 = math.sqrt(E0 / math.pi)
+        for i in range(25):
+            pe = beta.sf((0.25 * i * sigma0 / ucap + 1) / 2)
+            assert abs(st["exceed"][i] / n - pe) < 4 * math.sqrt(pe * (1 - pe) / n) + 1e-9
+        # mean pair energy s_k is 1/K for every mode, and the s_k sum to one
+        assert abs(st["spectrum"].sum() - n) < 1e-6 * n
+        assert np.all(np.abs(st["spectrum"] / n - 1 / K) < 4 * math.sqrt(1 / K / n))
+
+
+def divided_difference_exp(ts):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    tab = [mp.e ** (-t) for t in ts]
+    for lvl in range(1, len(ts)):
+        tab = [(tab[i + 1] - tab[i]) / (ts[i + lvl] - ts[i]) for i in range(len(ts) - lvl)]
+    return tab[0]
+
+
+def Z_linear(K, bp):
+    """E_mu0[exp(-beta' S/K^2)]: under mu0 the pair energies s_k are Dirichlet(1,..,1),
+    so by Hermite-Genocchi the mean is (K-1)! (-1)^(K-1) times the divided
+    difference of exp(-x) at the nodes beta' k^2/K^2."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    ts = [mp.mpf(bp) * k * k / K**2 for k in range(1, K + 1)]
+    return float(mp.factorial(K - 1) * (-1) ** (K - 1) * divided_difference_exp(ts))
+
+
+@pytest.mark.parametrize("K,bp", [(16, 20.0), (8, 40.0)])
+def test_linear_acceptance_closed_form(K, bp):
+    """r = 0 acceptance in closed form for both proposals; the paper proposal
+    accepts Prod_k w_k Z / M (g = Prod w_k Q^-K against mu0)."""
+    Z = Z_linear(K, bp)
+    a = O.alpha_star(K, bp)
+    w = [1 + a * bp * k * k / K**3 for k in range(1, K + 1)]
+    acc_u = Z * math.exp(bp / K**2)
+    acc_p = Z * float(np.prod(w)) * math.exp(-logM_r0_paper(K, bp))
+    for prop, acc in ((O.UNIFORM, acc_u), (O.PAPER, acc_p)):
+        pt = O.make_point(K, 1.0, bp, 0.0, prop)
+        pt.logM = O.log_M(pt, 0)
+        n = 1 << 20
+        st = O.run_stats(pt, 77, 0, 0, n)
+        p = st["n_acc"] / n
+        assert abs(p - acc) < 4 * math.sqrt(acc * (1 - acc) / n), (prop, p, acc)
+        assert st["n_viol"] == 0
+    if (K, bp) == (16, 20.0):  # Table 1, first row: acceptance 0.95
+        assert abs(acc_p - 0.95) < 0.01
+
+
+ROWS = [(16, 20.0, 60.0), (16, 40.0, 30.0), (16, 60.0, 20.0), (16, 20.0, 0.0),
+        (32, 20.0, 0.0), (32, 40.0, 75.0)]
+
+
+@pytest.mark.parametrize("K,bp,r", ROWS)
+def test_paper_table_rows(K, bp, r):
+    """Tables 1-2: acceptance of the paper proposal and ensemble skewness of the
+    surface displacement (all 2K grid values of every accepted field)."""
+    table = GOLD["table1_K16"]["rows"] if K == 16 else GOLD["table2_K32"]["rows"]
+    row = [x for x in table if x[0] == bp and x[1] == r][0]
+    skew_ref, acc_ref = row[2], row[3]
+    pt = O.make_point(K, 1.0, bp, r, O.PAPER)
+    pt.logM = O.log_M(pt, 2)
+    n = 1 << (20 if acc_ref > 0.1 else 21)
+    st = O.run_stats(pt, 5, 0, 0, n)
+    p = st["n_acc"] / n
+    se = math.sqrt(p * (1 - p) / n)
+    # paper values carry two digits and the paper's own M: 3 SE + 10 %
+    assert abs(p - acc_ref) < 3 * se + 0.1 * acc_ref, (p, acc_ref)
+    m = O.moments(st["n_acc"] * 2 * K, st["sum_grid"])
+    se_s = math.sqrt(6.0 / st["n_acc"])
+    assert abs(m["skew"] - skew_ref) < 3 * se_s + 0.005, (m["skew"], skew_ref)
+    assert st["n_viol"] == 0 and st["max_delta"] <= 0
+    ucap = math.sqrt(2 * K / math.pi)
+    assert int(np.sum(st["hist"])) == st["n_acc"]
+
+
+def test_four_sigma_threshold():
+    assert abs(4 * math.sqrt(1.0 / math.pi) - GOLD["four_sigma_E0_1"]["value"]) < 0.005
