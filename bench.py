@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 rejection sampler for the truncated-KdV Gibbs measure.
+
+Workload (default): K = 32 modes, grid N = 128, E0 = 1, eight beta' values
+log-spaced over [20, 60] with beta' C3/C2 = 9000 (the extreme-event regime of
+Table 2), 2^28 proposals per point and step, all eight points in one
+persistent launch.  A step is one such run of the whole hot path.
+
+Prints one JSON line (rank 0).  `value` is accepted samples per second of the
+whole job; proposals per second and the per-form numbers are alongside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("accepted samples/sec and proposals/sec at K=32 "
+          "(learned+BF16-split vs plain FP32, 1 GB300)")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alg_ops_per_proposal(K: int) -> int:
+    """Ideal thread-instruction count of one proposal of the FP32 triad form:
+    Philox4x32-10 (ceil(K/2)+1 blocks x 10 rounds x 4: two wide multiplies and
+    two 3-input xors), Box-Muller and scaling (20 per mode), the |x|^2, S, Q,
+    u0 accumulations (4 per mode), the symmetric double sum of Eq. (42)
+    (4 FMA per pair k < n-k, 3 for the middle term, 4 for the outer update),
+    and 40 for log Q, ln U, the ratio and the decision."""
+    blocks = (K + 1) // 2 + 1
+    triad = sum(4 * ((n - 1) // 2) + (3 if n % 2 == 0 else 0) + 4 for n in range(2, K + 1))
+    return 40 * blocks + 20 * K + 4 * K + triad + 40
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_points(rank, n_per_point):
+    from paper_2411_16952_gb300 import workloads
+    wl = workloads.extreme_k32(n_per_point)
+    # each rank samples its own streams (point ids rank*8 + p): disjoint draws
+    return wl, [(bp, r, rank * len(wl["points"]) + p) for p, (bp, r) in enumerate(wl["points"])]
+
+
+def cpu_baseline(wl, pts, seconds=15.0, sample_points=2):
+    """The FP64 oracle, as it stands, on all host cores, on a bounded sample:
+    the first `sample_points` points of the workload, sized to ~`seconds`."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    K, E0 = wl["K"], wl["E0"]
+    ops = []
+    for bp, r, pid in pts[:sample_points]:
+        pt = O.make_point(K, E0, bp, r, O.PAPER)
+        from paper_2411_16952_gb300 import tkdv_log_M
+        pt.logM = tkdv_log_M(K, bp, E0, r, np.array(pt.sigma2[:K]))
+        ops.append((pt, pid))
+    t0 = time.perf_counter()
+    O.run_stats(ops[0][0], 0, ops[0][1], 0, 1 << 18, cores)
+    per = (time.perf_counter() - t0) / (1 << 18)
+    n = int(max(1 << 18, min(1 << 30, seconds / max(per, 1e-12) / len(ops))))
+    acc = prop = 0
+    t0 = time.perf_counter()
+    for pt, pid in ops:
+        st = O.run_stats(pt, 0, pid, 0, n, cores)
+        acc += st["n_acc"]
+        prop += st["n_prop"]
+    dt = time.perf_counter() - t0
+    return {"value": acc / dt, "unit": "accepted samples/s", "proposals_per_s": prop / dt,
+            "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": "%d proposals of each of the first %d points (K=%d, paper proposal), FP64 C oracle, "
+                      "%d threads" % (n, len(ops), K, cores)}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, per step a bounded
+    sample of the same workload (one point per step, cycling)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2411_16952_gb300 import workloads
+    wl = workloads.extreme_k32(1)
+    K, E0 = wl["K"], wl["E0"]
+    cores = os.cpu_count() or 1
+    pts = []
+    for p, (bp, r) in enumerate(wl["points"]):
+        pt = O.make_point(K, E0, bp, r, O.PAPER)
+        pt.logM = O.log_M(pt, 0) if args.ref_exact_envelope else _lib_envelope(K, bp, E0, r, pt)
+        pts.append((pt, p))
+    n = args.ref_proposals
+    for i in range(args.warmup):
+        pt, pid = pts[i % len(pts)]
+        O.run_stats(pt, 0, pid, 0, n, cores)
+    acc = prop = 0
+    t_all = 0.0
+    for i in range(args.steps):
+        pt, pid = pts[i % len(pts)]
+        t0 = time.perf_counter()
+        st = O.run_stats(pt, 0, pid, (i + 1) * n, n, cores)
+        t_all += time.perf_counter() - t0
+        acc += st["n_acc"]
+        prop += st["n_prop"]
+    val = acc / t_all
+    line = {"metric": METRIC, "value": val, "unit": "accepted samples/s", "impl": "reference",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "proposals_per_s": prop / t_all,
+            "config": {"workload": wl["name"], "K": K, "points": len(pts),
+                       "proposals_per_step": n, "proposal": "paper"},
+            "cpu_baseline": {"value": val, "unit": "accepted samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d proposals per step, one point per step (cycling over %d), "
+                                       "FP64 C oracle on %d threads" % (n, len(pts), cores)},
+            "e2e": {"value": val, "unit": "accepted samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _lib_envelope(K, bp, E0, r, pt):
+    """The oracle needs log M; use its own Nelder-Mead (slow at K = 32) unless
+    a cached value is present in tests/golden/envelopes.json."""
+    import oracle as O
+    path = os.path.join(ROOT, "tests", "golden", "envelopes.json")
+    if os.path.exists(path):
+        key = "K%d_E%.17g_b%.17g_r%.17g_p%d" % (K, E0, bp, r, O.PAPER)
+        pts = json.load(open(path))["points"]
+        if key in pts:
+            return pts[key]["logM"]
+    return O.log_M(pt, 0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-per-point", type=int, default=1 << 28)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-proposals", type=int, default=1 << 22)
+    ap.add_argument("--ref-exact-envelope", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2411_16952_gb300 as T
+    from paper_2411_16952_gb300 import _build
+    _build.build()
+    peaks, peak_src = measured_peaks()
+    wl, pts = workload_points(rank, args.n_per_point)
+    K, E0, n = wl["K"], wl["E0"], args.n_per_point
+    stream = torch.cuda.current_stream()
+    points = [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=pid) for bp, r, pid in pts]
+    S = T.Sampler(K, points, sample_capacity=1 << 21, stream=stream)
+    if not args.no_autotune:
+        S.autotune(1 << 22)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    seed = 0
+    for _ in range(args.warmup):
+        S.run(n, seed)
+    S.sync()
+    S.reset()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the step events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.run(n, seed)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    st = S.stats()
+    acc = sum(s["n_accepted"] for s in st)
+    prop = sum(s["n_proposals"] for s in st)
+    t_s = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        cnt = torch.tensor([acc, prop], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(cnt)
+        t_s, acc, prop = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
+    launch = S.launch_config()
+
+    # ---- end to end through the public API with host buffers ------------
+    S.reset()
+    rec_bytes = T.tkdv_record_bytes(K)
+    host_rec = np.zeros(1 << 21 * 1, dtype=np.uint8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    e2e_acc = 0
+    for i in range(args.steps):
+        S.reset()
+        S.run(n, seed + 1 + i)
+        sts = S.stats()
+        recs = S.samples(1 << 21)
+        e2e_acc += sum(s["n_accepted"] for s in sts)
+        d2h += len(recs["idx"]) * rec_bytes + len(sts) * 2304
+    e2e_t = time.perf_counter() - t0
+    S.close()
+
+    ops = alg_ops_per_proposal(K)
+    step_s = t_s / args.steps
+    achieved = ops * (prop / args.steps) / step_s / 1e12
+    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": acc / t_s, "unit": "accepted samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "proposals_per_s": prop / t_s,
+        "acceptance": acc / max(prop, 1),
+        "forms": {"triad_f32_paper": {"accepted_per_s": acc / t_s, "proposals_per_s": prop / t_s}},
+        "config": {"workload": wl["name"], "K": K, "grid_N": wl["grid_N"], "points": len(pts),
+                   "proposals_per_point_per_step": n, "form": "triad_f32", "proposal": "paper",
+                   "l2": "256 MiB buffer written between timed steps, outside the step events",
+                   "launch": launch, "parallelism": "points x index ranges, weak per GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "ops_per_proposal": ops,
+                     "note": "ideal thread-instruction count per proposal; peak = 152 SM x 128 lanes x "
+                             "max SM clock (%s sm_max_mhz)" % peak_src},
+        "e2e": {"value": e2e_acc / e2e_t, "unit": "accepted samples/s",
+                "h2d_bytes_per_step": 8 * 2 * len(pts) + 8, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, pts, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * tkdv.h - C ABI of the GB300 (sm_103a) rejection sampler for the
+ * truncated-KdV (TKdV) Gibbs measure of Moore & Foerster, "In search of rogue
+ * waves: a novel proposal distribution for parallelized rejection sampling of
+ * the truncated KdV Gibbs measure" (arXiv 2411.16952).
+ *
+ * What one proposal does (Sec. IV.B of the paper):
+ *   draw X ~ gamma_Sigma, the anisotropic Gaussian of Eqs. (24)-(26)
+ *   (or X ~ gamma, Eq. 14, for the uniform proposal of Eq. 15);
+ *   project X^ = X/|X| onto the energy sphere S^{2K-1};
+ *   compute log f/(M g) by Eq. (40) with H2 (Eq. 20), H3 (Eq. 42 or the grid
+ *   cubature of Eq. 2) and beta H (Eq. 43);
+ *   accept with probability f/(M g); an accepted X^ is a wave field through
+ *   Eq. (16).
+ *
+ * Conventions used throughout
+ *   - K in [1, 64] complex modes; a state is the real vector
+ *     xhat = [xhat_1..xhat_K | xhat_{K+1}..xhat_{2K}] (cosine half | sine
+ *     half), u_k = sqrt(E0/2pi) (xhat_k - i xhat_{K+k}) (Eq. 16).
+ *   - r is the ratio C3/C2 of Eq. (43).  Together with K, E0 and beta' it is
+ *     the full parameter set of the method (Sec. IV.A).
+ *   - Random stream (the paper names none): Philox4x32-10 with key
+ *     (seed_lo, seed_hi) and counter (block j, idx_lo, idx_hi, point_id).
+ *     Mode k takes the Box-Muller pair in words 2h, 2h+1 of block
+ *     j = (k-1)/2, h = (k-1) % 2 (cosine -> X_k, sine -> X_{K+k}).  The accept
+ *     uniform is word 0 of block ceil(K/2).  A word w maps to
+ *     (2 floor(w/512) + 1) 2^-24.  Accept iff ln U < log f/(M g).
+ *     Given (parameters, seed, point_id, log M) the accepted set of an index
+ *     range is therefore a fixed set, whatever the launch shape.
+ *   - Return values: 0 on success, a negative TKDV_ERR_* code otherwise;
+ *     sampler_last_error() then holds a one-line message.  No entry point
+ *     aborts the process or falls back to a CPU path.
+ *   - Ownership: a sampler handle owns every device buffer it allocates
+ *     (cudaMalloc at create time); the caller owns every host buffer it
+ *     passes in.  All calls on one handle must come from one host thread at
+ *     a time.
+ */
+#ifndef TKDV_H
+#define TKDV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define TKDV_OK 0
+#define TKDV_ERR_INVALID_ARG (-1) /* parameter out of range (message says which) */
+#define TKDV_ERR_NO_ALPHA (-2)    /* paper proposal with beta' >= K^2 sum 1/k^2: Eq. (29) has no root */
+#define TKDV_ERR_CUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error string) */
+#define TKDV_ERR_OOM (-4)         /* cudaMalloc / cudaMallocHost failed */
+#define TKDV_ERR_TIMEOUT (-5)     /* a device wait hit its iteration limit; results of that run are void */
+#define TKDV_ERR_UNSUPPORTED (-6) /* requested form not available on this device */
+#define TKDV_ERR_ENVELOPE (-7)    /* envelope search failed (non-finite log M) */
+
+/* ---- proposal kinds (Sec. III) ------------------------------------------ */
+#define TKDV_PROPOSAL_UNIFORM 0 /* uniform measure mu0 on the sphere (Eq. 15); the naive baseline */
+#define TKDV_PROPOSAL_PAPER 1   /* projected anisotropic Gaussian, sigma_k^2 of Eq. (25) at alpha* */
+#define TKDV_PROPOSAL_LEARNED 2 /* paper sigma_k^2 times exp(c_k), c_k given per point (see tkdv_point) */
+
+/* ---- H3 forms ------------------------------------------------------------ */
+#define TKDV_H3_TRIAD_F32 0   /* double sum of Eq. (42) on FP32 CUDA cores */
+#define TKDV_H3_GRID_BF16X3 1 /* grid cubature of Eq. (2) as a tensor-core contraction, BF16 hi/lo x3 */
+
+#define TKDV_MAX_POINTS 64
+#define TKDV_HIST_BINS 256
+#define TKDV_N_EXCEED 25
+
+/* One parameter point (Sec. IV.A: K, E0, beta', C3/C2 are the only parameters). */
+typedef struct {
+    double beta_p;  /* normalised inverse temperature beta' (Eq. 21), >= 0 */
+    double E0;      /* energy (Eq. 5), > 0 */
+    double r;       /* C3/C2 (Eq. 43), any real */
+    int proposal;   /* TKDV_PROPOSAL_* */
+    uint32_t point_id;  /* fourth Philox counter word for this point */
+    int override_logM;  /* 1: use logM below instead of the library's envelope search */
+    double logM;        /* log of the rejection constant M of Eq. (45) when overridden */
+    /* TKDV_PROPOSAL_LEARNED only: host array of K per-mode log-variance
+       corrections c_k (k = 1..K); sigma_k^2 = sigma_k^2(paper) * exp(c_k).
+       Copied at create time; may be NULL for the other proposals. */
+    const double *log_var_correction;
+} tkdv_point;
+
+/* Options shared by all points of one handle. */
+typedef struct {
+    int K;                    /* modes, 1..64, common to all points of the handle */
+    int h3_mode;              /* TKDV_H3_* */
+    int grid_N;               /* grid points for TKDV_H3_GRID_BF16X3: multiple of 16, > 3K, <= 256 */
+    uint64_t sample_capacity; /* accepted records kept per handle (ring; excess is counted, not kept) */
+    void *cuda_stream;        /* cudaStream_t to launch on; NULL: the handle makes its own */
+    int use_graph;            /* 1: launch each run as one CUDA graph (default), 0: plain launches */
+    int ctas_per_sm;          /* 0: occupancy maximum; else persistent CTAs per SM */
+    int threads_per_cta;      /* 0: default (256); 128 or 256 */
+} tkdv_options;
+
+/* Statistics of one point, accumulated over runs until sampler_reset().
+   u0 = u(xi = 0) of each accepted field (Eq. 8). */
+typedef struct {
+    uint64_t n_proposals;
+    uint64_t n_accepted;
+    uint64_t n_near_threshold;      /* |ln U - log f/(Mg)| < 1e-6 (decided in FP64) */
+    uint64_t n_refined;             /* proposals decided on the FP64 path (guard band) */
+    uint64_t n_envelope_violations; /* proposals with log f/(Mg) > 0: M was too small */
+    uint64_t n_dropped;             /* accepted records that did not fit the ring */
+    uint64_t n_fallback;            /* guard-band proposals decided in FP32 because the FP64
+                                       queue was full (0 unless a run queued > 4M of them) */
+    double max_delta;               /* largest log f/(Mg) seen (FP32 path) */
+    double logM;                    /* envelope used */
+    double alpha_star;              /* root of Eq. (29) (paper / learned proposals), else 1 */
+    double sum_u0[4];               /* sum over accepted of u0^p, p = 1..4 */
+    double mean, var, skew, kurt;   /* of u0 over accepted samples */
+    uint64_t hist[TKDV_HIST_BINS];  /* u0 histogram on [hist_lo, hist_hi] */
+    double hist_lo, hist_hi;        /* -/+ sqrt(2 K E0 / pi), the largest |u| on the sphere */
+    uint64_t exceed[TKDV_N_EXCEED]; /* accepted with u0 > 0.25 i sqrt(E0/pi), i = 0..24 (Sec. V.D) */
+} tkdv_stats;
+
+/* Accepted-sample record, as stored in the device ring and returned by
+   sampler_samples(): this 32-byte header followed by float xhat[2K], the
+   projected state in [cosine | sine] order; records are
+   tkdv_record_bytes(K) bytes apart (16-byte multiple). */
+typedef struct {
+    uint64_t idx;    /* proposal index within its point's stream */
+    uint32_t point;  /* point number within the handle (0-based) */
+    uint32_t flags;  /* bit 0: decided on the FP64 path; bit 1: near threshold */
+    float H2, H3;    /* Eqs. (20) and (42) of the accepted state */
+    float u0;        /* u(xi = 0) */
+    float delta;     /* log f/(M g) */
+} tkdv_record;
+
+size_t tkdv_record_bytes(int K);
+
+typedef struct tkdv_sampler tkdv_sampler;
+
+/* sampler_create: one parameter point with default options (K given here,
+   triad H3, 2^20-record ring, own stream).  Runs the per-point precompute of
+   Sec. IV.B on the host: alpha* (Eq. 29), sigma_k (Eq. 25) and log M
+   (Eq. 45), then allocates device buffers.  The 4th argument is C3/C2.
+   Errors: INVALID_ARG (K outside 1..64, E0 <= 0, beta' < 0, unknown
+   proposal), NO_ALPHA, OOM, CUDA.  *out is NULL on error. */
+int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv_sampler **out);
+
+/* sampler_create_ex: n_points (1..64) points sharing opt->K and opt->h3_mode,
+   run together by one persistent launch (batched form).  Errors as above,
+   plus UNSUPPORTED for the grid form on a device without tcgen05. */
+int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options *opt,
+                      tkdv_sampler **out);
+
+/* sampler_run: n_proposals new proposals for every point, continuing each
+   point's index where the previous run stopped.  Asynchronous on the
+   handle's stream: returns after the launch; statistics accumulate on the
+   device.  Errors: INVALID_ARG, CUDA, TIMEOUT (from an earlier run). */
+int sampler_run(tkdv_sampler *h, uint64_t n_proposals, uint64_t seed);
+
+/* sampler_run_budgets: budgets[p] proposals for point p (uneven budgets). */
+int sampler_run_budgets(tkdv_sampler *h, const uint64_t *budgets, uint64_t seed);
+
+/* sampler_run_ranges: proposals idx0[p] .. idx0[p] + count[p] - 1 of every
+   point p; does not move the points' running index. */
+int sampler_run_ranges(tkdv_sampler *h, const uint64_t *idx0, const uint64_t *count, uint64_t seed);
+
+/* sampler_stats: waits for the handle's stream, then fills out[p] for
+   p = 0..n_out-1 (n_out <= number of points).  Moments are reduced from
+   exact 64-bit fixed-point sums (u0^p scaled by 2^28, 2^24, 2^20, 2^16). */
+int sampler_stats(tkdv_sampler *h, tkdv_stats *out, int n_out);
+
+/* sampler_samples: waits, then copies up to max_records accepted records
+   (tkdv_record_bytes(K) bytes each, unordered) to dst, a host buffer if
+   dst_on_device == 0, else a device buffer; *n_out = records copied. */
+int sampler_samples(tkdv_sampler *h, void *dst, int dst_on_device, uint64_t max_records,
+                    uint64_t *n_out);
+
+/* sampler_reset: zero statistics, the record ring and the running indices. */
+int sampler_reset(tkdv_sampler *h);
+
+/* sampler_sync: wait for all work queued on the handle's stream; returns
+   TIMEOUT if a device wait of any earlier run gave up. */
+int sampler_sync(tkdv_sampler *h);
+
+/* sampler_set_deadline_ns: time budget of every persistent CTA in later
+   runs (0 = none).  A CTA past its budget takes no further chunk; the run
+   then ends early and sampler_sync / sampler_stats return TKDV_ERR_TIMEOUT
+   once (the flag is cleared when reported).  Statistics hold the proposals
+   that did run. */
+int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns);
+
+/* sampler_point_info: alpha*, log M and the K proposal variances sigma_k^2
+   (Eq. 25, or the learned ones) of point p; any output may be NULL. */
+int sampler_point_info(tkdv_sampler *h, int p, double *alpha_star, double *logM, double *sigma2);
+
+/* sampler_replay: per-proposal outputs of point p for the n host-listed
+   indices (a test and debugging path that runs the same device code as the
+   sampler).  out is a host array of n * (8 + 2K) doubles per proposal:
+   [delta, lnU, accept, flags, H2, H3, u0, S, xhat_1..xhat_2K]. */
+int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint64_t seed,
+                   double *out);
+
+/* sampler_autotune: time the persistent launch on `calib_proposals` per point
+   for each candidate (CTAs per SM, threads per CTA, chunk size) and keep the
+   fastest for later runs.  Resets statistics afterwards.  *best_us receives
+   the best time (may be NULL). */
+int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us);
+
+/* sampler_launch_config: the launch shape of the next run. */
+int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk);
+
+const char *sampler_last_error(const tkdv_sampler *h);
+void sampler_destroy(tkdv_sampler *h);
+
+/* ---- host precompute, exported for tests --------------------------------- */
+/* alpha* = root of F(alpha) = 1 - (alpha/K) sum_k 1/(1 + alpha beta' k^2/K^3)
+   (Eq. 29).  Errors: INVALID_ARG, NO_ALPHA. */
+int tkdv_alpha_star(int K, double beta_p, double *out);
+
+/* log M = max over the sphere of log f/g (Eq. 45), searched from the
+   Dirichlet kernel of Eq. (46) and other starts.  sigma2 (K values) gives the
+   pair variances for the Gaussian proposals; NULL for the uniform proposal. */
+int tkdv_log_M(int K, double beta_p, double E0, double r, const double *sigma2, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TKDV_H */

@@ -1,0 +1,339 @@
+"""GB300 (sm_103a) rejection sampler for the truncated-KdV Gibbs measure.
+
+Python binding of the C ABI in include/tkdv.h (argument marshalling only:
+every step of the sampler runs in the library's CUDA kernels).  The functions
+carry the C names (``sampler_create``, ``sampler_run``, ``sampler_stats`` ...);
+:class:`Sampler` wraps one handle.  PyTorch is used only to hand the library a
+CUDA stream (``torch.cuda.current_stream()``) and device buffers for records.
+
+The shared library is built by ``__graft_entry__.build()`` (or
+``paper_2411_16952_gb300._build.build()``).  There is no fallback: if
+libtkdv.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtkdv.so")
+
+TKDV_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NO_ALPHA", -3: "CUDA", -4: "OOM", -5: "TIMEOUT",
+          -6: "UNSUPPORTED", -7: "ENVELOPE"}
+PROPOSAL_UNIFORM, PROPOSAL_PAPER, PROPOSAL_LEARNED = 0, 1, 2
+H3_TRIAD_F32, H3_GRID_BF16X3 = 0, 1
+MAX_POINTS = 64
+HIST_BINS = 256
+N_EXCEED = 25
+
+EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler_run",
+            "sampler_run_budgets", "sampler_run_ranges", "sampler_stats", "sampler_samples",
+            "sampler_reset", "sampler_sync", "sampler_set_deadline_ns", "sampler_point_info",
+            "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
+            "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M"]
+
+
+class TkdvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class tkdv_point(C.Structure):
+    _fields_ = [("beta_p", C.c_double), ("E0", C.c_double), ("r", C.c_double),
+                ("proposal", C.c_int), ("point_id", C.c_uint32), ("override_logM", C.c_int),
+                ("logM", C.c_double), ("log_var_correction", C.POINTER(C.c_double))]
+
+
+class tkdv_options(C.Structure):
+    _fields_ = [("K", C.c_int), ("h3_mode", C.c_int), ("grid_N", C.c_int),
+                ("sample_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
+                ("use_graph", C.c_int), ("ctas_per_sm", C.c_int), ("threads_per_cta", C.c_int)]
+
+
+class tkdv_stats(C.Structure):
+    _fields_ = [("n_proposals", C.c_uint64), ("n_accepted", C.c_uint64),
+                ("n_near_threshold", C.c_uint64), ("n_refined", C.c_uint64),
+                ("n_envelope_violations", C.c_uint64), ("n_dropped", C.c_uint64),
+                ("n_fallback", C.c_uint64), ("max_delta", C.c_double), ("logM", C.c_double),
+                ("alpha_star", C.c_double), ("sum_u0", C.c_double * 4), ("mean", C.c_double),
+                ("var", C.c_double), ("skew", C.c_double), ("kurt", C.c_double),
+                ("hist", C.c_uint64 * HIST_BINS), ("hist_lo", C.c_double), ("hist_hi", C.c_double),
+                ("exceed", C.c_uint64 * N_EXCEED)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libtkdv.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libtkdv.so is not built; run __graft_entry__.build() first")
+            L = C.CDLL(LIB_PATH)
+            vp, u64, i, d = C.c_void_p, C.c_uint64, C.c_int, C.c_double
+            dp, u64p = C.POINTER(C.c_double), C.POINTER(C.c_uint64)
+            L.tkdv_record_bytes.argtypes = [i]
+            L.tkdv_record_bytes.restype = C.c_size_t
+            L.sampler_create.argtypes = [i, d, d, d, i, C.POINTER(vp)]
+            L.sampler_create_ex.argtypes = [C.POINTER(tkdv_point), i, C.POINTER(tkdv_options),
+                                            C.POINTER(vp)]
+            L.sampler_run.argtypes = [vp, u64, u64]
+            L.sampler_run_budgets.argtypes = [vp, u64p, u64]
+            L.sampler_run_ranges.argtypes = [vp, u64p, u64p, u64]
+            L.sampler_stats.argtypes = [vp, C.POINTER(tkdv_stats), i]
+            L.sampler_samples.argtypes = [vp, vp, i, u64, u64p]
+            L.sampler_reset.argtypes = [vp]
+            L.sampler_sync.argtypes = [vp]
+            L.sampler_set_deadline_ns.argtypes = [vp, u64]
+            L.sampler_point_info.argtypes = [vp, i, dp, dp, dp]
+            L.sampler_replay.argtypes = [vp, i, u64p, u64, u64, dp]
+            L.sampler_autotune.argtypes = [vp, u64, dp]
+            L.sampler_launch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_uint32)]
+            L.sampler_last_error.argtypes = [vp]
+            L.sampler_last_error.restype = C.c_char_p
+            L.sampler_destroy.argtypes = [vp]
+            L.sampler_destroy.restype = None
+            L.tkdv_alpha_star.argtypes = [i, d, dp]
+            L.tkdv_log_M.argtypes = [i, d, d, d, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _check(rc, handle=None):
+    if rc != TKDV_OK:
+        msg = lib().sampler_last_error(handle)
+        raise TkdvError(rc, msg.decode() if msg else "")
+
+
+# ---- the C entry points under their own names ------------------------------
+def tkdv_record_bytes(K):
+    return int(lib().tkdv_record_bytes(K))
+
+
+def tkdv_alpha_star(K, beta_p):
+    out = C.c_double()
+    _check(lib().tkdv_alpha_star(K, beta_p, C.byref(out)))
+    return out.value
+
+
+def tkdv_log_M(K, beta_p, E0, r, sigma2=None):
+    out = C.c_double()
+    s2 = None
+    if sigma2 is not None:
+        arr = np.ascontiguousarray(np.asarray(sigma2, dtype=np.float64))
+        s2 = arr.ctypes.data_as(C.POINTER(C.c_double))
+    _check(lib().tkdv_log_M(K, beta_p, E0, r, s2, C.byref(out)))
+    return out.value
+
+
+def sampler_create(K, beta_p, E0, r, proposal):
+    h = C.c_void_p()
+    _check(lib().sampler_create(K, beta_p, E0, r, proposal, C.byref(h)))
+    return h
+
+
+def sampler_create_ex(points, options):
+    arr = (tkdv_point * len(points))(*points)
+    h = C.c_void_p()
+    _check(lib().sampler_create_ex(arr, len(points), C.byref(options), C.byref(h)))
+    return h
+
+
+def sampler_run(h, n_proposals, seed):
+    _check(lib().sampler_run(h, n_proposals, seed), h)
+
+
+def sampler_run_budgets(h, budgets, seed):
+    b = np.ascontiguousarray(np.asarray(budgets, dtype=np.uint64))
+    _check(lib().sampler_run_budgets(h, b.ctypes.data_as(C.POINTER(C.c_uint64)), seed), h)
+
+
+def sampler_run_ranges(h, idx0, count, seed):
+    a = np.ascontiguousarray(np.asarray(idx0, dtype=np.uint64))
+    b = np.ascontiguousarray(np.asarray(count, dtype=np.uint64))
+    _check(lib().sampler_run_ranges(h, a.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    b.ctypes.data_as(C.POINTER(C.c_uint64)), seed), h)
+
+
+def sampler_stats(h, n_points):
+    out = (tkdv_stats * n_points)()
+    _check(lib().sampler_stats(h, out, n_points), h)
+    return [_stats_dict(out[p]) for p in range(n_points)]
+
+
+def sampler_samples(h, K, max_records, device_dst=None):
+    """Accepted records: a dict of numpy arrays (host), or, with device_dst (a
+    torch uint8 CUDA tensor of max_records * record_bytes), the record count
+    after a device-to-device copy into it."""
+    n = C.c_uint64()
+    rb = tkdv_record_bytes(K)
+    if device_dst is not None:
+        _check(lib().sampler_samples(h, C.c_void_p(device_dst.data_ptr()), 1, max_records,
+                                     C.byref(n)), h)
+        return int(n.value)
+    buf = np.zeros(max(1, max_records) * rb, dtype=np.uint8)
+    _check(lib().sampler_samples(h, buf.ctypes.data_as(C.c_void_p), 0, max_records, C.byref(n)), h)
+    return decode_records(buf[: int(n.value) * rb], K)
+
+
+def sampler_reset(h):
+    _check(lib().sampler_reset(h), h)
+
+
+def sampler_sync(h):
+    _check(lib().sampler_sync(h), h)
+
+
+def sampler_set_deadline_ns(h, ns):
+    _check(lib().sampler_set_deadline_ns(h, ns), h)
+
+
+def sampler_point_info(h, p, K):
+    a, lm = C.c_double(), C.c_double()
+    s2 = np.zeros(K)
+    _check(lib().sampler_point_info(h, p, C.byref(a), C.byref(lm),
+                                    s2.ctypes.data_as(C.POINTER(C.c_double))), h)
+    return a.value, lm.value, s2
+
+
+def sampler_replay(h, p, K, idx, seed):
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    n = int(idx.size)
+    out = np.zeros((max(n, 1), 8 + 2 * K))
+    _check(lib().sampler_replay(h, p, idx.ctypes.data_as(C.POINTER(C.c_uint64)), n, seed,
+                                out.ctypes.data_as(C.POINTER(C.c_double))), h)
+    out = out[:n]
+    return {"delta": out[:, 0], "lnU": out[:, 1], "accept": out[:, 2] > 0.5,
+            "flags": out[:, 3].astype(np.int64), "H2": out[:, 4], "H3": out[:, 5],
+            "u0": out[:, 6], "S": out[:, 7], "xhat": out[:, 8:]}
+
+
+def sampler_autotune(h, calib_proposals):
+    us = C.c_double()
+    _check(lib().sampler_autotune(h, calib_proposals, C.byref(us)), h)
+    return us.value
+
+
+def sampler_launch_config(h):
+    c, t, ch = C.c_int(), C.c_int(), C.c_uint32()
+    _check(lib().sampler_launch_config(h, C.byref(c), C.byref(t), C.byref(ch)), h)
+    return {"ctas": c.value, "threads": t.value, "chunk": ch.value}
+
+
+def sampler_last_error(h=None):
+    m = lib().sampler_last_error(h)
+    return m.decode() if m else ""
+
+
+def sampler_destroy(h):
+    if h:
+        lib().sampler_destroy(h)
+
+
+# ---- helpers ---------------------------------------------------------------
+def _stats_dict(s):
+    return {"n_proposals": s.n_proposals, "n_accepted": s.n_accepted,
+            "n_near_threshold": s.n_near_threshold, "n_refined": s.n_refined,
+            "n_envelope_violations": s.n_envelope_violations, "n_dropped": s.n_dropped,
+            "n_fallback": s.n_fallback, "max_delta": s.max_delta, "logM": s.logM,
+            "alpha_star": s.alpha_star, "sum_u0": np.array(s.sum_u0[:]), "mean": s.mean,
+            "var": s.var, "skew": s.skew, "kurt": s.kurt,
+            "hist": np.array(s.hist[:], dtype=np.uint64), "hist_lo": s.hist_lo,
+            "hist_hi": s.hist_hi, "exceed": np.array(s.exceed[:], dtype=np.uint64)}
+
+
+def decode_records(buf, K):
+    rb = tkdv_record_bytes(K)
+    n = len(buf) // rb
+    raw = np.frombuffer(bytes(buf), dtype=np.uint8).reshape(n, rb) if n else np.zeros((0, rb), np.uint8)
+    return {"idx": raw[:, 0:8].copy().view(np.uint64).reshape(n),
+            "point": raw[:, 8:12].copy().view(np.uint32).reshape(n),
+            "flags": raw[:, 12:16].copy().view(np.uint32).reshape(n),
+            "H2": raw[:, 16:20].copy().view(np.float32).reshape(n),
+            "H3": raw[:, 20:24].copy().view(np.float32).reshape(n),
+            "u0": raw[:, 24:28].copy().view(np.float32).reshape(n),
+            "delta": raw[:, 28:32].copy().view(np.float32).reshape(n),
+            "xhat": raw[:, 32:32 + 8 * K].copy().view(np.float32).reshape(n, 2 * K)}
+
+
+def make_point(beta_p, E0, r, proposal=PROPOSAL_PAPER, point_id=0, logM=None, log_var_correction=None):
+    p = tkdv_point()
+    p.beta_p, p.E0, p.r, p.proposal, p.point_id = beta_p, E0, r, proposal, point_id
+    if logM is not None:
+        p.override_logM, p.logM = 1, float(logM)
+    if log_var_correction is not None:
+        arr = np.ascontiguousarray(np.asarray(log_var_correction, dtype=np.float64))
+        p._keep = arr  # keep alive until create copies it
+        p.log_var_correction = arr.ctypes.data_as(C.POINTER(C.c_double))
+    return p
+
+
+class Sampler:
+    """One handle of the C library (several parameter points, one K)."""
+
+    def __init__(self, K, points, h3_mode=H3_TRIAD_F32, grid_N=0, sample_capacity=1 << 20,
+                 stream=None, use_graph=True, ctas_per_sm=0, threads_per_cta=0):
+        self.K = K
+        self.n_points = len(points)
+        o = tkdv_options()
+        o.K, o.h3_mode, o.grid_N = K, h3_mode, grid_N
+        o.sample_capacity = sample_capacity
+        o.cuda_stream = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        o.use_graph = 1 if use_graph else 0
+        o.ctas_per_sm, o.threads_per_cta = ctas_per_sm, threads_per_cta
+        self.h = sampler_create_ex(points, o)
+
+    def run(self, n_proposals, seed):
+        sampler_run(self.h, n_proposals, seed)
+
+    def run_budgets(self, budgets, seed):
+        sampler_run_budgets(self.h, budgets, seed)
+
+    def run_ranges(self, idx0, count, seed):
+        sampler_run_ranges(self.h, idx0, count, seed)
+
+    def stats(self):
+        return sampler_stats(self.h, self.n_points)
+
+    def samples(self, max_records=1 << 20, device_dst=None):
+        return sampler_samples(self.h, self.K, max_records, device_dst)
+
+    def reset(self):
+        sampler_reset(self.h)
+
+    def sync(self):
+        sampler_sync(self.h)
+
+    def set_deadline_ns(self, ns):
+        sampler_set_deadline_ns(self.h, ns)
+
+    def point_info(self, p=0):
+        return sampler_point_info(self.h, p, self.K)
+
+    def replay(self, p, idx, seed):
+        return sampler_replay(self.h, p, self.K, idx, seed)
+
+    def autotune(self, calib_proposals=1 << 22):
+        return sampler_autotune(self.h, calib_proposals)
+
+    def launch_config(self):
+        return sampler_launch_config(self.h)
+
+    def close(self):
+        if self.h:
+            sampler_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,555 @@
+// sampler_impl.cuh - device code of the rejection sampler (Sec. IV.B of
+// Moore & Foerster, arXiv 2411.16952): one proposal per thread, everything in
+// registers, a persistent CTA loop over chunks of proposal indices.
+//
+// Per proposal (FP32 fast path):
+//   1. Philox4x32-10 words for proposal idx (stream layout in include/tkdv.h);
+//   2. Box-Muller pairs -> the 2K standard normals of Eq. (14);
+//   3. scale by sigma_k (Eqs. 24-26); |x|^2, S|x|^2 and Q|x|^2 accumulate as
+//      the normals are made, so the projection xhat = x/|x| (Sec. IV.B) is
+//      applied as scalar factors, never to the 2K components;
+//   4. H3 by the double sum of Eq. (42) with the k <-> n-k symmetry folded;
+//   5. log f/(M g) = -beta' S/K^2 + beta' r/(E0 K^2) H3 + K ln Q - log M
+//      (Eqs. 40 and 43);
+//   6. accept iff ln U < log f/(M g).  The FP32 result decides only when the
+//      two sides differ by more than a rounding-error bound ("guard"); inside
+//      the guard band the proposal is queued and decided in FP64 by
+//      k_refine (same draw, same formulas).  So every decision equals the
+//      one an exact evaluation takes, up to FP64 rounding.
+//   7. warp-ballot compaction of accepted records into a ring, and streaming
+//      statistics of u(0) (Sec. V) in shared memory, flushed per chunk with
+//      integer atomics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "tkdv_internal.h"
+
+namespace tkdv {
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) ------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (2 floor(w/512) + 1) 2^-24: (w >> 8) | 1 == 2 floor(w/512) + 1, exact in FP32.
+__device__ __forceinline__ float u01f(uint32_t w) {
+    return __uint2float_rn((w >> 8) | 1u) * 0x1p-24f;
+}
+__device__ __forceinline__ double u01d(uint32_t w) {
+    return (double)((w >> 8) | 1u) * 0x1p-24;
+}
+
+// Order-preserving map float -> uint32 (for atomicMax on signed floats).
+__device__ __forceinline__ uint32_t fkey(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Scalar constants of the current point, held in registers.
+struct Scal {
+    float cS, cH, cQ, logM, u0s, h3s, E0, ga, gr, gh, ha, hb, ea;
+    uint32_t pid;
+    int K;
+};
+
+__device__ __forceinline__ Scal load_scal(const PointConst *P) {
+    Scal s;
+    s.cS = __ldg(&P->cS);
+    s.cH = __ldg(&P->cH);
+    s.cQ = __ldg(&P->cQ);
+    s.logM = __ldg(&P->logM_f);
+    s.u0s = __ldg(&P->u0s);
+    s.h3s = __ldg(&P->h3s);
+    s.E0 = __ldg(&P->E0);
+    s.ga = __ldg(&P->guard_abs);
+    s.gr = __ldg(&P->guard_rel);
+    s.gh = __ldg(&P->guard_h);
+    s.ha = __ldg(&P->hist_a);
+    s.hb = __ldg(&P->hist_b);
+    s.ea = __ldg(&P->exc_a);
+    s.pid = __ldg(&P->point_id);
+    s.K = __ldg(&P->K);
+    return s;
+}
+
+// State of one proposal on the fast path: x, y are the scaled (unprojected)
+// cosine and sine halves of mode m = 0..KMAX-1.
+template <int KMAX>
+struct Draw {
+    float x[KMAX], y[KMAX];
+    float nrm2;   // |x|^2
+    float Sraw;   // sum k^2 (x_k^2 + y_k^2)  = S |x|^2
+    float zz;     // sum over active modes of the normals' squares = Q |x|^2
+    float u0raw;  // sum_k x_k                = u(0) |x| / u0s
+};
+
+// Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
+template <int KMAX, bool UNIF>
+__device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
+                                          uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
+                                          uint32_t k0, uint32_t k1) {
+    d.nrm2 = 0.f;
+    d.Sraw = 0.f;
+    d.zz = 0.f;
+    d.u0raw = 0.f;
+#pragma unroll
+    for (int j = 0; j < (KMAX + 1) / 2; ++j) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, idx_lo, idx_hi, pid), k0, k1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * j + h;
+            if (m < KMAX) {
+                const float u1 = u01f(h ? w.z : w.x);
+                const float u2 = u01f(h ? w.w : w.y);
+                const float rho = -2.f * logf(u1);
+                const float rad = sqrtf(rho);
+                float sn, cs;
+                sincospif(2.f * u2, &sn, &cs);
+                const float s = UNIF ? act[m] : sig[m];
+                const float sr = s * rad;
+                const float xm = sr * cs, ym = sr * sn;
+                d.x[m] = xm;
+                d.y[m] = ym;
+                const float sk = (s * s) * rho;
+                d.nrm2 += sk;
+                d.Sraw = fmaf((float)((m + 1) * (m + 1)), sk, d.Sraw);
+                d.zz = fmaf(act[m], rho, d.zz);
+                d.u0raw += xm;
+            }
+        }
+    }
+}
+
+// Step 4: T = sum_{n=2}^{KMAX} x_n A_n + y_n B_n, with
+//   A_n = sum_{k=1}^{n-1} x_k x_{n-k} - y_k y_{n-k},
+//   B_n = sum_{k=1}^{n-1} x_k y_{n-k} + y_k x_{n-k},
+// i.e. Re(conj(v_n) sum v_k v_{n-k}) for v = x - i y (Eq. 42 up to 2 pi c^3).
+template <int KMAX, typename R>
+__device__ __forceinline__ R triad(const R *x, const R *y) {
+    R T = R(0);
+#pragma unroll
+    for (int n = 2; n <= KMAX; ++n) {
+        R A = R(0), Bv = R(0);
+#pragma unroll
+        for (int k = 1; 2 * k < n; ++k) {
+            A = fma(x[k - 1], x[n - k - 1], A);
+            A = fma(-y[k - 1], y[n - k - 1], A);
+            Bv = fma(x[k - 1], y[n - k - 1], Bv);
+            Bv = fma(y[k - 1], x[n - k - 1], Bv);
+        }
+        A = A + A;
+        Bv = Bv + Bv;
+        if ((n & 1) == 0) {
+            const int h = n / 2;
+            A = fma(x[h - 1], x[h - 1], A);
+            A = fma(-y[h - 1], y[h - 1], A);
+            Bv = fma(x[h - 1] + x[h - 1], y[h - 1], Bv);
+        }
+        T = fma(x[n - 1], A, T);
+        T = fma(y[n - 1], Bv, T);
+    }
+    return T;
+}
+
+struct Fast {
+    float delta, lnU, d, guard, S, T, inv;
+};
+
+// Steps 4-6 on the fast path.
+template <int KMAX, bool UNIF>
+__device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, uint32_t wacc) {
+    Fast f;
+    const float inv2 = 1.f / dr.nrm2;
+    f.inv = rsqrtf(dr.nrm2);
+    f.S = dr.Sraw * inv2;
+    f.T = triad<KMAX, float>(dr.x, dr.y) * (inv2 * f.inv);
+    const float tS = c.cS * f.S;
+    const float tH = c.cH * f.T;
+    const float tQ = UNIF ? 0.f : c.cQ * logf(dr.zz * inv2);
+    f.delta = ((tS + tH) + tQ) - c.logM;
+    f.lnU = logf(u01f(wacc));
+    f.d = f.lnU - f.delta;
+    f.guard = c.ga + c.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(f.lnU) + fabsf(c.logM)) + c.gh;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t accept_word(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
+                                                int K, uint32_t k0, uint32_t k1) {
+    return philox4x32_10(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), k0, k1).x;
+}
+
+__device__ __forceinline__ int hist_bin(float u0, float a, float b) {
+    int v = __float2int_rd(fmaf(u0, a, b));
+    return min(max(v, 0), kHistBins - 1);
+}
+__device__ __forceinline__ int exc_bin(float u0, float a) {
+    if (!(u0 > 0.f)) return 0;
+    int v = __float2int_ru(u0 * a);
+    return min(v, kExcBins - 1);
+}
+
+// ---- FP64 evaluation of one proposal (guard band, replay) -----------------
+struct Out64 {
+    double delta, lnU, S, T;
+    float H2, H3, u0;
+    int accept, near;
+};
+
+// The same draw and the same formulas as the fast path, in FP64.  xh (may be
+// null) receives the projected state [cos | sin] as floats.
+template <int KMAX, bool UNIF>
+__device__ __noinline__ void eval64(const PointConst *P, unsigned long long idx, uint32_t k0,
+                                    uint32_t k1, Out64 *o, float *xh) {
+    const int K = P->K;
+    const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32), pid = P->point_id;
+    double x[KMAX], y[KMAX];
+    double nrm2 = 0.0, Sraw = 0.0, zz = 0.0, u0raw = 0.0;
+    for (int m = 0; m < KMAX; ++m) {
+        x[m] = 0.0;
+        y[m] = 0.0;
+    }
+    for (int m = 0; m < K; ++m) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(m / 2), lo, hi, pid), k0, k1);
+        const int h = m & 1;
+        const double u1 = u01d(h ? w.z : w.x), u2 = u01d(h ? w.w : w.y);
+        const double rho = -2.0 * log(u1);
+        const double rad = sqrt(rho);
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const double s = UNIF ? 1.0 : P->sigma_d[m];
+        x[m] = s * rad * cs;
+        y[m] = s * rad * sn;
+        const double sk = x[m] * x[m] + y[m] * y[m];
+        nrm2 += sk;
+        Sraw += (double)((m + 1) * (m + 1)) * sk;
+        zz += rho;
+        u0raw += x[m];
+    }
+    double T = 0.0;
+    for (int n = 2; n <= K; ++n) {
+        double A = 0.0, Bv = 0.0;
+        for (int k = 1; k <= n - 1; ++k) {
+            A += x[k - 1] * x[n - k - 1] - y[k - 1] * y[n - k - 1];
+            Bv += x[k - 1] * y[n - k - 1] + y[k - 1] * x[n - k - 1];
+        }
+        T += x[n - 1] * A + y[n - 1] * Bv;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    const double inv2 = inv * inv;
+    o->S = Sraw * inv2;
+    o->T = T * inv2 * inv;
+    double delta = P->cS_d * o->S + P->cH_d * o->T;
+    if (!UNIF) delta += P->cQ_d * log(zz * inv2);
+    delta -= P->logM;
+    const uint32_t wa = accept_word(lo, hi, pid, K, k0, k1);
+    o->delta = delta;
+    o->lnU = log(u01d(wa));
+    o->accept = o->lnU < delta;
+    o->near = fabs(o->lnU - delta) < 1e-6;
+    o->H2 = (float)((double)P->E0 * o->S);
+    o->H3 = (float)((double)P->h3s * o->T);
+    o->u0 = (float)((double)P->u0s * u0raw * inv);
+    if (xh) {
+        for (int m = 0; m < K; ++m) {
+            xh[m] = (float)(x[m] * inv);
+            xh[K + m] = (float)(y[m] * inv);
+        }
+    }
+}
+
+// Write one accepted record.
+template <int KMAX>
+__device__ __forceinline__ void write_record(unsigned char *rec, unsigned long long idx, uint32_t point,
+                                             uint32_t flags, float H2, float H3, float u0, float delta,
+                                             const float *x, const float *y, float inv, int K) {
+    *reinterpret_cast<unsigned long long *>(rec) = idx;
+    uint32_t *h = reinterpret_cast<uint32_t *>(rec + 8);
+    h[0] = point;
+    h[1] = flags;
+    float *f = reinterpret_cast<float *>(rec + 16);
+    f[0] = H2;
+    f[1] = H3;
+    f[2] = u0;
+    f[3] = delta;
+    float *xh = f + 4;
+#pragma unroll
+    for (int m = 0; m < KMAX; ++m) {
+        if (m < K) {
+            xh[m] = x[m] * inv;
+            xh[K + m] = y[m] * inv;
+        }
+    }
+}
+
+// ---- the persistent sampler ----------------------------------------------
+template <int KMAX, bool UNIF, int NT>
+__global__ void __launch_bounds__(NT) k_sample_triad(DevBufs B, RunArgs A, uint32_t k0, uint32_t k1) {
+    __shared__ uint32_t s_hist[kHistBins];
+    __shared__ uint32_t s_exc[kExcBins];
+    __shared__ unsigned long long s_q[4];
+    __shared__ uint32_t s_cnt[4];  // accepted, envelope violations, dropped, fallbacks
+    __shared__ uint32_t s_maxd;
+    __shared__ uint32_t s_chunk;
+    __shared__ float s_sig[KMAX], s_act[KMAX];
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
+    if (tid < kExcBins) s_exc[tid] = 0;
+    if (tid < 4) {
+        s_q[tid] = 0ull;
+        s_cnt[tid] = 0;
+    }
+    if (tid == 0) s_maxd = 0;
+    const uint32_t total = A.chunk_prefix[A.n_points];
+    const unsigned long long t0 = A.deadline_ns ? globaltimer_ns() : 0ull;
+
+    for (;;) {
+        if (tid == 0) {
+            uint32_t c = atomicAdd(&B.counters[0], 1u);
+            if (A.deadline_ns && c < total && globaltimer_ns() - t0 > A.deadline_ns) {
+                atomicOr(B.status, kStatusDeadline);
+                c = total;
+            }
+            s_chunk = c;
+        }
+        __syncthreads();
+        const uint32_t c = s_chunk;
+        if (c >= total) break;
+        int p = 0;
+        while (p + 1 < A.n_points && A.chunk_prefix[p + 1] <= c) ++p;
+        const unsigned long long local = (unsigned long long)(c - A.chunk_prefix[p]) * A.chunk;
+        const unsigned long long left = A.count[p] - local;
+        const uint32_t n_here = left < A.chunk ? (uint32_t)left : A.chunk;
+        const unsigned long long base = A.idx0[p] + local;
+        const PointConst *P = B.pts + p;
+        if (tid < KMAX) {
+            s_sig[tid] = __ldg(&P->sigma[tid]);
+            s_act[tid] = __ldg(&P->act[tid]);
+        }
+        const Scal sc = load_scal(P);
+        __syncthreads();
+
+        float maxd = -INFINITY;
+        for (uint32_t i0 = 0; i0 < n_here; i0 += NT) {
+            const uint32_t i = i0 + (uint32_t)tid;
+            const bool valid = i < n_here;
+            const unsigned long long idx = base + i;
+            const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
+            Draw<KMAX> dr;
+            draw_fast<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, k0, k1);
+            const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
+            const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
+            bool defer = valid && fabsf(f.d) < f.guard;
+            if (valid) maxd = fmaxf(maxd, f.delta);
+
+            // guard band -> FP64 queue
+            const unsigned md = __ballot_sync(0xffffffffu, defer);
+            if (md) {
+                const int leader = __ffs(md) - 1;
+                uint32_t slot0 = 0;
+                if (lane == leader) slot0 = atomicAdd(&B.counters[1], (uint32_t)__popc(md));
+                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                if (defer) {
+                    const uint32_t slot = slot0 + __popc(md & ((1u << lane) - 1u));
+                    if (slot < B.refine_cap) {
+                        RefineItem it;
+                        it.idx = idx;
+                        it.point = (uint32_t)p;
+                        it.pad = 0;
+                        B.refine[slot] = it;
+                    } else {  // queue full: decide in FP32 and flag the run
+                        atomicOr(B.status, kStatusRefineOverflow);
+                        atomicAdd(&s_cnt[3], 1u);
+                        defer = false;
+                    }
+                }
+            }
+            const bool acc = valid && !defer && f.d < 0.f;
+            if (valid && !defer && f.delta > 0.f) atomicAdd(&s_cnt[1], 1u);
+
+            const unsigned ma = __ballot_sync(0xffffffffu, acc);
+            if (ma) {
+                const int leader = __ffs(ma) - 1;
+                unsigned long long slot0 = 0;
+                if (lane == leader) {
+                    slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(ma));
+                    atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
+                }
+                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                if (acc) {
+                    const float u0 = sc.u0s * dr.u0raw * f.inv;
+                    atomicAdd(&s_hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
+                    atomicAdd(&s_exc[exc_bin(u0, sc.ea)], 1u);
+                    const float u2 = u0 * u0;
+                    atomicAdd(&s_q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
+                    atomicAdd(&s_q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
+                    atomicAdd(&s_q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+                    atomicAdd(&s_q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+                    const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
+                    if (slot < B.ring_cap) {
+                        write_record<KMAX>(B.ring + slot * B.rec_bytes, idx, (uint32_t)p, 0u, sc.E0 * f.S,
+                                           sc.h3s * f.T, u0, f.delta, dr.x, dr.y, f.inv, sc.K);
+                    } else {
+                        atomicAdd(&s_cnt[2], 1u);
+                    }
+                }
+            }
+        }
+        // chunk done: flush this CTA's partials into the point's StatBlock
+        uint32_t key = fkey(maxd);
+        key = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0 && maxd > -INFINITY) atomicMax(&s_maxd, key);
+        __syncthreads();
+        StatBlock *st = B.stats + p;
+        for (int e = tid; e < kHistBins; e += NT) {
+            if (s_hist[e]) {
+                atomicAdd(&st->hist[e], (unsigned long long)s_hist[e]);
+                s_hist[e] = 0;
+            }
+        }
+        if (tid < kExcBins && s_exc[tid]) {
+            atomicAdd(&st->exc[tid], (unsigned long long)s_exc[tid]);
+            s_exc[tid] = 0;
+        }
+        if (tid < 4 && s_q[tid]) {
+            atomicAdd(&st->q[tid], s_q[tid]);
+            s_q[tid] = 0ull;
+        }
+        if (tid == 0) {
+            atomicAdd(&st->n_prop, (unsigned long long)n_here);
+            if (s_cnt[0]) atomicAdd(&st->n_acc, (unsigned long long)s_cnt[0]);
+            if (s_cnt[1]) atomicAdd(&st->n_viol, (unsigned long long)s_cnt[1]);
+            if (s_cnt[2]) atomicAdd(&st->n_dropped, (unsigned long long)s_cnt[2]);
+            if (s_cnt[3]) atomicAdd(&st->n_fallback, (unsigned long long)s_cnt[3]);
+            if (s_maxd) atomicMax(&st->maxd_key, (unsigned long long)s_maxd);
+            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+            s_maxd = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- FP64 decision of the guard-band proposals ---------------------------
+template <int KMAX, bool UNIF>
+__global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t k1) {
+    const uint32_t n = min(*(volatile uint32_t *)&B.counters[1], B.refine_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const RefineItem it = B.refine[i];
+        const PointConst *P = B.pts + it.point;
+        StatBlock *st = B.stats + it.point;
+        Out64 o;
+        float xh[2 * KMAX];
+        eval64<KMAX, UNIF>(P, it.idx, k0, k1, &o, xh);
+        atomicAdd(&st->n_refined, 1ull);
+        if (o.near) atomicAdd(&st->n_near, 1ull);
+        if (o.delta > 0.0) atomicAdd(&st->n_viol, 1ull);
+        if (!o.accept) continue;
+        atomicAdd(&st->n_acc, 1ull);
+        const float u0 = o.u0;
+        atomicAdd(&st->hist[hist_bin(u0, __ldg(&P->hist_a), __ldg(&P->hist_b))], 1ull);
+        atomicAdd(&st->exc[exc_bin(u0, __ldg(&P->exc_a))], 1ull);
+        const float u2 = u0 * u0;
+        atomicAdd(&st->q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
+        atomicAdd(&st->q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
+        atomicAdd(&st->q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+        atomicAdd(&st->q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+        const unsigned long long slot = atomicAdd(B.ring_count, 1ull);
+        if (slot < B.ring_cap) {
+            const int K = P->K;
+            unsigned char *rec = B.ring + slot * B.rec_bytes;
+            *reinterpret_cast<unsigned long long *>(rec) = it.idx;
+            uint32_t *h = reinterpret_cast<uint32_t *>(rec + 8);
+            h[0] = it.point;
+            h[1] = 1u | (o.near ? 2u : 0u);
+            float *f = reinterpret_cast<float *>(rec + 16);
+            f[0] = o.H2;
+            f[1] = o.H3;
+            f[2] = o.u0;
+            f[3] = (float)o.delta;
+            for (int m = 0; m < 2 * K; ++m) f[4 + m] = xh[m];
+        } else {
+            atomicAdd(&st->n_dropped, 1ull);
+        }
+    }
+}
+
+// ---- replay: per-proposal outputs of listed indices -----------------------
+// out row: [delta, lnU, accept, flags, H2, H3, u0, S, xhat(2K)]
+template <int KMAX, bool UNIF>
+__global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsigned long long *idx,
+                                               unsigned long long n, uint32_t k0, uint32_t k1,
+                                               double *out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Scal sc = load_scal(P);
+    const int K = sc.K;
+    const unsigned long long id = idx[i];
+    const uint32_t lo = (uint32_t)id, hi = (uint32_t)(id >> 32);
+    Draw<KMAX> dr;
+    draw_fast<KMAX, UNIF>(dr, P->sigma, P->act, lo, hi, sc.pid, k0, k1);
+    const uint32_t wa = accept_word(lo, hi, sc.pid, K, k0, k1);
+    const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
+    double *row = out + i * (unsigned long long)(8 + 2 * K);
+    if (fabsf(f.d) < f.guard) {
+        Out64 o;
+        float xh[2 * KMAX];
+        eval64<KMAX, UNIF>(P, id, k0, k1, &o, xh);
+        row[0] = o.delta;
+        row[1] = o.lnU;
+        row[2] = o.accept;
+        row[3] = 1.0 + (o.near ? 2.0 : 0.0);
+        row[4] = o.H2;
+        row[5] = o.H3;
+        row[6] = o.u0;
+        row[7] = o.S;
+        for (int m = 0; m < 2 * K; ++m) row[8 + m] = xh[m];
+        return;
+    }
+    row[0] = f.delta;
+    row[1] = f.lnU;
+    row[2] = f.d < 0.f ? 1.0 : 0.0;
+    row[3] = 0.0;
+    row[4] = sc.E0 * f.S;
+    row[5] = sc.h3s * f.T;
+    row[6] = sc.u0s * dr.u0raw * f.inv;
+    row[7] = f.S;
+#pragma unroll
+    for (int m = 0; m < KMAX; ++m) {
+        if (m < K) {
+            row[8 + m] = dr.x[m] * f.inv;
+            row[8 + K + m] = dr.y[m] * f.inv;
+        }
+    }
+}
+
+template <int KMAX>
+void fill_triad_kernels(TriadKernels *t) {
+    t->main[0][0] = (const void *)k_sample_triad<KMAX, false, 128>;
+    t->main[0][1] = (const void *)k_sample_triad<KMAX, false, 256>;
+    t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128>;
+    t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256>;
+    t->refine[0] = (const void *)k_refine<KMAX, false>;
+    t->refine[1] = (const void *)k_refine<KMAX, true>;
+    t->replay[0] = (const void *)k_replay<KMAX, false>;
+    t->replay[1] = (const void *)k_replay<KMAX, true>;
+}
+
+}  // namespace tkdv

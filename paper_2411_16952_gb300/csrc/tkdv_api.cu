@@ -1,0 +1,668 @@
+// tkdv_api.cu - the C ABI of include/tkdv.h: handle life cycle, per-point
+// precompute, the launch of one run (memset -> persistent sampler -> FP64
+// guard-band pass, as one CUDA graph), statistics and records.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tkdv.h"
+#include "tkdv_internal.h"
+
+using namespace tkdv;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Launch {
+    int threads = 256;
+    int ctas = 0;
+};
+
+}  // namespace
+
+struct tkdv_sampler {
+    int K = 0, kmax = 0, n_points = 0;
+    tkdv_options opt{};
+    std::vector<tkdv_point> pts;
+    std::vector<double> alpha, logM;
+    std::vector<std::vector<double>> sigma2;
+    std::vector<PointConst> pc;
+    std::vector<unsigned long long> next_idx;
+    bool all_uniform = false;
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevBufs dev{};
+    void *d_pts = nullptr, *d_stats = nullptr, *d_ring = nullptr, *d_ring_count = nullptr,
+         *d_refine = nullptr, *d_counters = nullptr, *d_status = nullptr;
+    size_t rec_bytes = 0;
+    TriadKernels kt{};
+    Launch launch;
+    unsigned long long deadline_ns = 0;
+    // graph of one run: memset(counters) -> sampler -> refine
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_main = nullptr, n_refine = nullptr;
+    Launch graph_launch;
+    // kernel arguments (the graph nodes point at copies made at update time)
+    RunArgs args{};
+    uint32_t key0 = 0, key1 = 0;
+    std::string err;
+};
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            h->err = std::string(#call) + " failed: " + cudaGetErrorString(e_);              \
+            return e_ == cudaErrorMemoryAllocation ? TKDV_ERR_OOM : TKDV_ERR_CUDA;            \
+        }                                                                                     \
+    } while (0)
+
+namespace {
+
+int fail(tkdv_sampler *h, int code, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int kmax_for(int K) {
+    for (int m : {4, 8, 16, 32, 64})
+        if (K <= m) return m;
+    return 0;
+}
+
+// Per-point precompute and the constant table of one point.
+int build_point(tkdv_sampler *h, int p, std::string &msg) {
+    const tkdv_point &q = h->pts[p];
+    const int K = h->K;
+    if (!(q.E0 > 0) || !std::isfinite(q.E0)) {
+        msg = "point " + std::to_string(p) + ": E0 must be > 0";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    if (!(q.beta_p >= 0) || !std::isfinite(q.beta_p)) {
+        msg = "point " + std::to_string(p) + ": beta' must be >= 0";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(q.r)) {
+        msg = "point " + std::to_string(p) + ": C3/C2 must be finite";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    if (q.proposal < 0 || q.proposal > 2) {
+        msg = "point " + std::to_string(p) + ": unknown proposal";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    if (q.proposal == TKDV_PROPOSAL_LEARNED && !q.log_var_correction) {
+        msg = "point " + std::to_string(p) + ": learned proposal needs log_var_correction";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    double alpha = 1.0;
+    std::vector<double> s2(K, 1.0);
+    if (q.proposal != TKDV_PROPOSAL_UNIFORM) {
+        int rc = tkdv_alpha_star(K, q.beta_p, &alpha);
+        if (rc != TKDV_OK) {
+            msg = "point " + std::to_string(p) + ": no root alpha* of F (beta' >= K^2 sum 1/k^2)";
+            return rc;
+        }
+        const double K3 = (double)K * K * K;
+        for (int k = 1; k <= K; ++k) {
+            s2[k - 1] = 1.0 / (1.0 + alpha * q.beta_p * (double)k * k / K3);  // Eq. (25)
+            if (q.proposal == TKDV_PROPOSAL_LEARNED) {
+                const double c = q.log_var_correction[k - 1];
+                if (!std::isfinite(c)) {
+                    msg = "point " + std::to_string(p) + ": non-finite log-variance correction";
+                    return TKDV_ERR_INVALID_ARG;
+                }
+                s2[k - 1] *= std::exp(c);
+            }
+        }
+    }
+    double lm = q.logM;
+    if (!q.override_logM) {
+        int rc = tkdv_log_M(K, q.beta_p, q.E0, q.r, q.proposal == TKDV_PROPOSAL_UNIFORM ? nullptr : s2.data(),
+                            &lm);
+        if (rc != TKDV_OK) {
+            msg = "point " + std::to_string(p) + ": envelope search failed";
+            return rc;
+        }
+    } else if (!std::isfinite(lm)) {
+        msg = "point " + std::to_string(p) + ": overridden log M is not finite";
+        return TKDV_ERR_INVALID_ARG;
+    }
+    h->alpha[p] = alpha;
+    h->logM[p] = lm;
+    h->sigma2[p] = s2;
+
+    PointConst c;
+    std::memset(&c, 0, sizeof(c));
+    for (int k = 0; k < kKMax; ++k) {
+        const bool on = k < K;
+        c.sigma[k] = on ? (float)std::sqrt(s2[k]) : 0.f;
+        c.sigma_d[k] = on ? std::sqrt(s2[k]) : 0.0;
+        c.act[k] = on ? 1.f : 0.f;
+    }
+    const double K2 = (double)K * K;
+    const double cc = std::sqrt(q.E0 / (2.0 * M_PI));
+    const double h3s = 2.0 * M_PI * cc * cc * cc;
+    c.cS_d = -q.beta_p / K2;                         // Eq. (43), H2 = E0 S
+    c.cH_d = q.beta_p * q.r / (q.E0 * K2) * h3s;     // Eq. (43), H3 = h3s T
+    c.cQ_d = q.proposal == TKDV_PROPOSAL_UNIFORM ? 0.0 : (double)K;  // Eq. (40) / (37)
+    c.logM = lm;
+    c.cS = (float)c.cS_d;
+    c.cH = (float)c.cH_d;
+    c.cQ = (float)c.cQ_d;
+    c.logM_f = (float)lm;
+    c.u0s = (float)(2.0 * cc);
+    c.h3s = (float)h3s;
+    c.E0 = (float)q.E0;
+    const double ucap = std::sqrt(2.0 * K * q.E0 / M_PI);
+    c.hist_a = (float)(kHistBins / (2.0 * ucap));
+    c.hist_b = (float)(kHistBins / 2);
+    c.exc_a = (float)(1.0 / (0.25 * std::sqrt(q.E0 / M_PI)));
+    // Guard band of the FP32 decision.  The FP32 value of log f/(Mg) carries
+    // the rounding of ~2K+16 chained operations on each term; T additionally
+    // sums O(K) products per mode with |T| <= sqrt(K) on the sphere.  The band
+    // is eight times that bound; proposals inside it are decided in FP64.
+    const double gam = 8.0 * (2.0 * K + 16.0) * std::ldexp(1.0, -24);
+    c.guard_abs = (float)(1e-6 + gam * std::fabs(c.cQ_d));
+    c.guard_rel = (float)gam;
+    c.guard_h = (float)(gam * std::fabs(c.cH_d) * std::sqrt((double)K));
+    c.point_id = q.point_id;
+    c.K = K;
+    h->pc[p] = c;
+    return TKDV_OK;
+}
+
+int set_default_launch(tkdv_sampler *h) {
+    const int uni = h->all_uniform ? 1 : 0;
+    const int thr = h->launch.threads;
+    const void *fn = h->kt.main[uni][thr == 128 ? 0 : 1];
+    int nb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, thr, 0));
+    if (nb < 1) return fail(h, TKDV_ERR_CUDA, "sampler kernel does not fit on an SM");
+    int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, nb) : nb;
+    h->launch.ctas = per_sm * h->num_sms;
+    return TKDV_OK;
+}
+
+// RunArgs for explicit ranges.
+int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned long long *count,
+               uint64_t seed) {
+    RunArgs &a = h->args;
+    std::memset(&a, 0, sizeof(a));
+    a.n_points = h->n_points;
+    unsigned long long total = 0;
+    for (int p = 0; p < h->n_points; ++p) {
+        a.idx0[p] = idx0[p];
+        a.count[p] = count[p];
+        total += count[p];
+    }
+    // about 8 chunks per persistent CTA, between 1 and 64 proposals per thread
+    const unsigned long long thr = (unsigned long long)h->launch.threads;
+    unsigned long long target = (total + 8ull * h->launch.ctas - 1) / (8ull * h->launch.ctas);
+    target = (target + thr - 1) / thr * thr;
+    target = std::max(thr, std::min(thr * 64ull, target));
+    a.chunk = (uint32_t)target;
+    unsigned long long acc = 0;
+    a.chunk_prefix[0] = 0;
+    for (int p = 0; p < h->n_points; ++p) {
+        acc += (count[p] + a.chunk - 1) / a.chunk;
+        if (acc >= 0xFFFFFFF0ull) return fail(h, TKDV_ERR_INVALID_ARG, "run too large (> 2^32 chunks)");
+        a.chunk_prefix[p + 1] = (uint32_t)acc;
+    }
+    a.deadline_ns = h->deadline_ns;
+    h->key0 = (uint32_t)seed;
+    h->key1 = (uint32_t)(seed >> 32);
+    return TKDV_OK;
+}
+
+int refine_grid(tkdv_sampler *h) { return std::max(1, h->num_sms * 4); }
+
+int build_graph(tkdv_sampler *h) {
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    if (h->graph) {
+        cudaGraphDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaMemsetParams ms{};
+    ms.dst = h->d_counters;
+    ms.value = 0;
+    ms.elementSize = 4;
+    ms.width = 2;
+    ms.height = 1;
+    ms.pitch = 0;
+    cudaGraphNode_t n_ms;
+    CK(cudaGraphAddMemsetNode(&n_ms, h->graph, nullptr, 0, &ms));
+    const int uni = h->all_uniform ? 1 : 0;
+    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)h->kt.main[uni][h->launch.threads == 128 ? 0 : 1];
+    kp.gridDim = dim3(h->launch.ctas);
+    kp.blockDim = dim3(h->launch.threads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = margs;
+    CK(cudaGraphAddKernelNode(&h->n_main, h->graph, &n_ms, 1, &kp));
+    void *rargs[] = {&h->dev, &h->key0, &h->key1};
+    cudaKernelNodeParams rp{};
+    rp.func = (void *)h->kt.refine[uni];
+    rp.gridDim = dim3(refine_grid(h));
+    rp.blockDim = dim3(128);
+    rp.kernelParams = rargs;
+    CK(cudaGraphAddKernelNode(&h->n_refine, h->graph, &h->n_main, 1, &rp));
+    CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+    h->graph_launch = h->launch;
+    return TKDV_OK;
+}
+
+int enqueue(tkdv_sampler *h) {
+    const int uni = h->all_uniform ? 1 : 0;
+    if (h->opt.use_graph) {
+        if (!h->exec || h->graph_launch.ctas != h->launch.ctas || h->graph_launch.threads != h->launch.threads) {
+            int rc = build_graph(h);
+            if (rc) return rc;
+        }
+        void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)h->kt.main[uni][h->launch.threads == 128 ? 0 : 1];
+        kp.gridDim = dim3(h->launch.ctas);
+        kp.blockDim = dim3(h->launch.threads);
+        kp.kernelParams = margs;
+        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->n_main, &kp));
+        void *rargs[] = {&h->dev, &h->key0, &h->key1};
+        cudaKernelNodeParams rp{};
+        rp.func = (void *)h->kt.refine[uni];
+        rp.gridDim = dim3(refine_grid(h));
+        rp.blockDim = dim3(128);
+        rp.kernelParams = rargs;
+        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->n_refine, &rp));
+        CK(cudaGraphLaunch(h->exec, h->stream));
+        return TKDV_OK;
+    }
+    CK(cudaMemsetAsync(h->d_counters, 0, 8, h->stream));
+    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
+    CK(cudaLaunchKernel(h->kt.main[uni][h->launch.threads == 128 ? 0 : 1], dim3(h->launch.ctas),
+                        dim3(h->launch.threads), margs, 0, h->stream));
+    void *rargs[] = {&h->dev, &h->key0, &h->key1};
+    CK(cudaLaunchKernel(h->kt.refine[uni], dim3(refine_grid(h)), dim3(128), rargs, 0, h->stream));
+    return TKDV_OK;
+}
+
+int run_ranges(tkdv_sampler *h, const unsigned long long *idx0, const unsigned long long *count,
+               uint64_t seed) {
+    unsigned long long total = 0;
+    for (int p = 0; p < h->n_points; ++p) total += count[p];
+    if (total == 0) return TKDV_OK;
+    int rc = build_args(h, idx0, count, seed);
+    if (rc) return rc;
+    return enqueue(h);
+}
+
+int check_status(tkdv_sampler *h) {
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, h->d_status, 4, cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(h->d_status, 0, 4));
+    if (st & (kStatusDeadline | kStatusMbarTimeout))
+        return fail(h, TKDV_ERR_TIMEOUT,
+                    (st & kStatusDeadline) ? "run stopped at its deadline" : "device wait timed out");
+    if (st & kStatusRefineOverflow)
+        h->err = "FP64 guard-band queue overflowed; the overflow was decided in FP32 (see n_fallback)";
+    return TKDV_OK;
+}
+
+void free_all(tkdv_sampler *h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (void *p : {h->d_pts, h->d_stats, h->d_ring, h->d_ring_count, h->d_refine, h->d_counters, h->d_status})
+        if (p) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tkdv_record_bytes(int K) { return record_bytes(K); }
+
+int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv_sampler **out) {
+    tkdv_point p{};
+    p.beta_p = beta_p;
+    p.E0 = E0;
+    p.r = r;
+    p.proposal = proposal;
+    tkdv_options o{};
+    o.K = K;
+    o.h3_mode = TKDV_H3_TRIAD_F32;
+    o.sample_capacity = 1ull << 20;
+    o.use_graph = 1;
+    return sampler_create_ex(&p, 1, &o, out);
+}
+
+int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options *opt, tkdv_sampler **out) {
+    if (!out) return fail(nullptr, TKDV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!points || !opt) return fail(nullptr, TKDV_ERR_INVALID_ARG, "points/options NULL");
+    if (n_points < 1 || n_points > kMaxPoints)
+        return fail(nullptr, TKDV_ERR_INVALID_ARG, "n_points must be in 1..64");
+    if (opt->K < 1 || opt->K > kKMax) return fail(nullptr, TKDV_ERR_INVALID_ARG, "K must be in 1..64");
+    if (opt->h3_mode != TKDV_H3_TRIAD_F32)
+        return fail(nullptr, TKDV_ERR_UNSUPPORTED, "only the FP32 triad form is built into this library");
+    if (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256)
+        return fail(nullptr, TKDV_ERR_INVALID_ARG, "threads_per_cta must be 0, 128 or 256");
+    tkdv_sampler *h = new tkdv_sampler();
+    h->K = opt->K;
+    h->kmax = kmax_for(opt->K);
+    h->n_points = n_points;
+    h->opt = *opt;
+    h->pts.assign(points, points + n_points);
+    h->alpha.assign(n_points, 1.0);
+    h->logM.assign(n_points, 0.0);
+    h->sigma2.assign(n_points, {});
+    h->pc.assign(n_points, PointConst{});
+    h->next_idx.assign(n_points, 0ull);
+    h->all_uniform = true;
+    for (int p = 0; p < n_points; ++p) {
+        std::string msg;
+        int rc = build_point(h, p, msg);
+        if (rc) {
+            delete h;
+            return fail(nullptr, rc, msg);
+        }
+        if (points[p].proposal != TKDV_PROPOSAL_UNIFORM) h->all_uniform = false;
+    }
+    switch (h->kmax) {
+        case 4: triad_kernels_k4(&h->kt); break;
+        case 8: triad_kernels_k8(&h->kt); break;
+        case 16: triad_kernels_k16(&h->kt); break;
+        case 32: triad_kernels_k32(&h->kt); break;
+        default: triad_kernels_k64(&h->kt); break;
+    }
+    auto bail = [&](int rc) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        h->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return bail(TKDV_ERR_CUDA);
+    }
+    h->launch.threads = opt->threads_per_cta ? opt->threads_per_cta : 256;
+    h->rec_bytes = record_bytes(h->K);
+    const unsigned long long cap = opt->sample_capacity;
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        cudaError_t ee = cudaMalloc(p, bytes ? bytes : 16);
+        if (ee != cudaSuccess) {
+            h->err = std::string("cudaMalloc: ") + cudaGetErrorString(ee);
+            return ee == cudaErrorMemoryAllocation ? TKDV_ERR_OOM : TKDV_ERR_CUDA;
+        }
+        return TKDV_OK;
+    };
+    int rc;
+    if ((rc = alloc(&h->d_pts, sizeof(PointConst) * n_points))) return bail(rc);
+    if ((rc = alloc(&h->d_stats, sizeof(StatBlock) * n_points))) return bail(rc);
+    if ((rc = alloc(&h->d_ring, h->rec_bytes * cap))) return bail(rc);
+    if ((rc = alloc(&h->d_ring_count, 8))) return bail(rc);
+    if ((rc = alloc(&h->d_refine, sizeof(RefineItem) * (size_t)kRefineCap))) return bail(rc);
+    if ((rc = alloc(&h->d_counters, 8))) return bail(rc);
+    if ((rc = alloc(&h->d_status, 4))) return bail(rc);
+    if (opt->cuda_stream) {
+        h->stream = (cudaStream_t)opt->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            h->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            return bail(TKDV_ERR_CUDA);
+        }
+        h->own_stream = true;
+    }
+    e = cudaMemcpy(h->d_pts, h->pc.data(), sizeof(PointConst) * n_points, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(StatBlock) * n_points);
+    if (e == cudaSuccess) e = cudaMemset(h->d_ring_count, 0, 8);
+    if (e == cudaSuccess) e = cudaMemset(h->d_counters, 0, 8);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 4);
+    if (e != cudaSuccess) {
+        h->err = std::string("initialising device buffers: ") + cudaGetErrorString(e);
+        return bail(TKDV_ERR_CUDA);
+    }
+    h->dev.pts = (const PointConst *)h->d_pts;
+    h->dev.stats = (StatBlock *)h->d_stats;
+    h->dev.ring = (unsigned char *)h->d_ring;
+    h->dev.ring_count = (unsigned long long *)h->d_ring_count;
+    h->dev.refine = (RefineItem *)h->d_refine;
+    h->dev.counters = (uint32_t *)h->d_counters;
+    h->dev.status = (uint32_t *)h->d_status;
+    h->dev.ring_cap = cap;
+    h->dev.rec_bytes = (uint32_t)h->rec_bytes;
+    h->dev.refine_cap = kRefineCap;
+    if ((rc = set_default_launch(h))) return bail(rc);
+    *out = h;
+    return TKDV_OK;
+}
+
+int sampler_run(tkdv_sampler *h, uint64_t n_proposals, uint64_t seed) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    std::vector<uint64_t> b(h->n_points, n_proposals);
+    return sampler_run_budgets(h, b.data(), seed);
+}
+
+int sampler_run_budgets(tkdv_sampler *h, const uint64_t *budgets, uint64_t seed) {
+    if (!h || !budgets) return TKDV_ERR_INVALID_ARG;
+    std::vector<unsigned long long> i0(h->n_points), c(h->n_points);
+    for (int p = 0; p < h->n_points; ++p) {
+        i0[p] = h->next_idx[p];
+        c[p] = budgets[p];
+    }
+    int rc = run_ranges(h, i0.data(), c.data(), seed);
+    if (rc) return rc;
+    for (int p = 0; p < h->n_points; ++p) h->next_idx[p] += budgets[p];
+    return TKDV_OK;
+}
+
+int sampler_run_ranges(tkdv_sampler *h, const uint64_t *idx0, const uint64_t *count, uint64_t seed) {
+    if (!h || !idx0 || !count) return TKDV_ERR_INVALID_ARG;
+    std::vector<unsigned long long> i0(idx0, idx0 + h->n_points), c(count, count + h->n_points);
+    return run_ranges(h, i0.data(), c.data(), seed);
+}
+
+int sampler_sync(tkdv_sampler *h) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
+int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    h->deadline_ns = ns;
+    return TKDV_OK;
+}
+
+int sampler_stats(tkdv_sampler *h, tkdv_stats *out, int n_out) {
+    if (!h || !out || n_out < 0 || n_out > h->n_points) return TKDV_ERR_INVALID_ARG;
+    int rc = sampler_sync(h);
+    std::vector<StatBlock> sb(h->n_points);
+    CK(cudaMemcpy(sb.data(), h->d_stats, sizeof(StatBlock) * h->n_points, cudaMemcpyDeviceToHost));
+    for (int p = 0; p < n_out; ++p) {
+        const StatBlock &s = sb[p];
+        tkdv_stats &o = out[p];
+        std::memset(&o, 0, sizeof(o));
+        o.n_proposals = s.n_prop;
+        o.n_accepted = s.n_acc;
+        o.n_near_threshold = s.n_near;
+        o.n_refined = s.n_refined;
+        o.n_envelope_violations = s.n_viol;
+        o.n_dropped = s.n_dropped;
+        o.n_fallback = s.n_fallback;
+        if (s.maxd_key == 0) {
+            o.max_delta = -INFINITY;
+        } else {
+            uint32_t k = (uint32_t)s.maxd_key;
+            uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+            float f;
+            std::memcpy(&f, &b, 4);
+            o.max_delta = f;
+        }
+        o.logM = h->logM[p];
+        o.alpha_star = h->alpha[p];
+        const double qs[4] = {kQ1, kQ2, kQ3, kQ4};
+        for (int q = 0; q < 4; ++q) o.sum_u0[q] = (double)(long long)s.q[q] / qs[q];
+        const double n = (double)s.n_acc;
+        if (n > 0) {
+            const double m1 = o.sum_u0[0] / n, m2 = o.sum_u0[1] / n, m3 = o.sum_u0[2] / n, m4 = o.sum_u0[3] / n;
+            o.mean = m1;
+            o.var = m2 - m1 * m1;
+            const double c3 = m3 - 3 * m1 * m2 + 2 * m1 * m1 * m1;
+            const double c4 = m4 - 4 * m1 * m3 + 6 * m1 * m1 * m2 - 3 * m1 * m1 * m1 * m1;
+            o.skew = c3 / std::pow(o.var, 1.5);
+            o.kurt = c4 / (o.var * o.var);
+        } else {
+            o.mean = o.var = o.skew = o.kurt = NAN;
+        }
+        for (int b = 0; b < kHistBins; ++b) o.hist[b] = s.hist[b];
+        const double ucap = std::sqrt(2.0 * h->K * h->pts[p].E0 / M_PI);
+        o.hist_lo = -ucap;
+        o.hist_hi = ucap;
+        for (int i = 0; i < TKDV_N_EXCEED; ++i) {
+            unsigned long long t = 0;
+            for (int e = i + 1; e < kExcBins; ++e) t += s.exc[e];
+            o.exceed[i] = t;
+        }
+    }
+    return rc;
+}
+
+int sampler_samples(tkdv_sampler *h, void *dst, int dst_on_device, uint64_t max_records, uint64_t *n_out) {
+    if (!h || (!dst && max_records) || !n_out) return TKDV_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long cnt = 0;
+    CK(cudaMemcpy(&cnt, h->d_ring_count, 8, cudaMemcpyDeviceToHost));
+    unsigned long long n = std::min<unsigned long long>(cnt, h->dev.ring_cap);
+    n = std::min<unsigned long long>(n, max_records);
+    if (n) CK(cudaMemcpy(dst, h->d_ring, n * h->rec_bytes, dst_on_device ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyDeviceToHost));
+    *n_out = n;
+    return TKDV_OK;
+}
+
+int sampler_reset(tkdv_sampler *h) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemset(h->d_stats, 0, sizeof(StatBlock) * h->n_points));
+    CK(cudaMemset(h->d_ring_count, 0, 8));
+    CK(cudaMemset(h->d_status, 0, 4));
+    std::fill(h->next_idx.begin(), h->next_idx.end(), 0ull);
+    return TKDV_OK;
+}
+
+int sampler_point_info(tkdv_sampler *h, int p, double *alpha_star, double *logM, double *sigma2) {
+    if (!h || p < 0 || p >= h->n_points) return TKDV_ERR_INVALID_ARG;
+    if (alpha_star) *alpha_star = h->alpha[p];
+    if (logM) *logM = h->logM[p];
+    if (sigma2)
+        for (int k = 0; k < h->K; ++k) sigma2[k] = h->sigma2[p][k];
+    return TKDV_OK;
+}
+
+int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint64_t seed, double *out) {
+    if (!h || p < 0 || p >= h->n_points || (!idx && n) || (!out && n)) return TKDV_ERR_INVALID_ARG;
+    if (n == 0) return TKDV_OK;
+    const size_t row = 8 + 2 * (size_t)h->K;
+    void *d_idx = nullptr, *d_out = nullptr;
+    CK(cudaMalloc(&d_idx, 8 * n));
+    cudaError_t e = cudaMalloc(&d_out, sizeof(double) * row * n);
+    if (e != cudaSuccess) {
+        cudaFree(d_idx);
+        return fail(h, TKDV_ERR_OOM, "replay buffers");
+    }
+    const int uni = h->all_uniform ? 1 : 0;
+    const PointConst *P = h->dev.pts + p;
+    unsigned long long nn = n;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    void *args[] = {(void *)&P, &d_idx, &nn, &k0, &k1, &d_out};
+    e = cudaMemcpyAsync(d_idx, idx, 8 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel(h->kt.replay[uni], dim3((unsigned)((n + 127) / 128)), dim3(128), args, 0, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double) * row * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_idx);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return fail(h, TKDV_ERR_CUDA, std::string("replay: ") + cudaGetErrorString(e));
+    return TKDV_OK;
+}
+
+int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us) {
+    if (!h || calib_proposals == 0) return TKDV_ERR_INVALID_ARG;
+    const int uni = h->all_uniform ? 1 : 0;
+    const int saved_graph = h->opt.use_graph;
+    h->opt.use_graph = 0;
+    std::vector<unsigned long long> i0(h->n_points, 1ull << 62), c(h->n_points, calib_proposals);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    Launch best = h->launch;
+    float best_ms = 1e30f;
+    for (int thr : {128, 256}) {
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, h->kt.main[uni][thr == 128 ? 0 : 1], thr, 0));
+        for (int per = 1; per <= nb; ++per) {
+            h->launch.threads = thr;
+            h->launch.ctas = per * h->num_sms;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CK(cudaEventRecord(e0, h->stream));
+                int rc = run_ranges(h, i0.data(), c.data(), 0x5EEDull + rep);
+                if (rc) return rc;
+                CK(cudaEventRecord(e1, h->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) ms_best = std::min(ms_best, ms);
+            }
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best = h->launch;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->launch = best;
+    h->opt.use_graph = saved_graph;
+    if (best_us) *best_us = best_ms * 1000.0;
+    return sampler_reset(h);
+}
+
+int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    if (ctas) *ctas = h->launch.ctas;
+    if (threads_per_cta) *threads_per_cta = h->launch.threads;
+    if (chunk) *chunk = h->args.chunk;
+    return TKDV_OK;
+}
+
+const char *sampler_last_error(const tkdv_sampler *h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void sampler_destroy(tkdv_sampler *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

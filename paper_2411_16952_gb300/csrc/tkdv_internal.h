@@ -1,0 +1,110 @@
+// tkdv_internal.h - structures shared by the host side of the library and its
+// CUDA kernels (not part of the public C ABI, see include/tkdv.h for that).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace tkdv {
+
+constexpr int kKMax = 64;
+constexpr int kMaxPoints = 64;
+constexpr int kHistBins = 256;
+constexpr int kExcBins = 26;  // exceed-bin e = number of thresholds 0.25 i sigma0 below u0
+constexpr uint32_t kRefineCap = 1u << 22;
+
+// Fixed-point scales of the u0^p moment sums (exact 64-bit integer sums).
+constexpr float kQ1 = 268435456.0f;  // 2^28
+constexpr float kQ2 = 16777216.0f;   // 2^24
+constexpr float kQ3 = 1048576.0f;    // 2^20
+constexpr float kQ4 = 65536.0f;      // 2^16
+
+// Per-point constants, built on the host from the precompute (alpha*, sigma_k,
+// log M) and read by every proposal of that point.
+struct PointConst {
+    float sigma[kKMax];     // sigma_k (k = 1..K), 0 beyond K (masks the mode out)
+    float act[kKMax];       // 1 for k <= K, else 0
+    double sigma_d[kKMax];  // sigma_k in FP64 for the guard-band recomputation
+    // log f/(M g) = cS * S + cH * T + cQ * ln Q - logM, where for xhat = x/|x|
+    //   S = sum k^2 s_k            (H2 = E0 S, Eq. 20)
+    //   T = sum_n Re(conj(v_n) sum_{k<n} v_k v_{n-k}), v_k = xh_k - i xh_{K+k}
+    //       (H3 = 2 pi (E0/2pi)^{3/2} T, Eq. 42)
+    //   Q = sum_k s_k / sigma_k^2  (Eq. 33 times 2; = 1 + alpha* beta' S/K^3 for Eq. 40)
+    float cS, cH, cQ, logM_f;
+    double cS_d, cH_d, cQ_d, logM;
+    float u0s;          // u(0) = u0s * sum_k xh_k, u0s = 2 sqrt(E0/2pi)   (Eq. 8)
+    float h3s;          // H3 = h3s * T, h3s = 2 pi (E0/2pi)^{3/2}
+    float E0;
+    float hist_a, hist_b;  // histogram bin = floor(u0 * hist_a + hist_b)
+    float exc_a;           // exceed bin = ceil(u0 * exc_a) for u0 > 0
+    float guard_abs, guard_rel, guard_h;  // FP32 decision guard (see sampler_impl.cuh)
+    uint32_t point_id;
+    int K;
+    int pad[2];
+};
+
+// Statistics of one point on the device: only integers, so that the result
+// does not depend on the order in which CTAs add to it.
+struct StatBlock {
+    unsigned long long n_prop, n_acc, n_near, n_refined, n_viol, n_dropped;
+    unsigned long long maxd_key;  // order-preserving key of the largest FP32 delta
+    unsigned long long q[4];      // sum of round(u0^p * kQScale[p-1]) (two's complement)
+    unsigned long long hist[kHistBins];
+    unsigned long long exc[kExcBins];
+    unsigned long long n_fallback;  // guard-band proposals decided in FP32 (queue full)
+    unsigned long long pad[2];
+};
+
+struct RefineItem {
+    unsigned long long idx;
+    uint32_t point;
+    uint32_t pad;
+};
+
+// Device buffers of one handle.
+struct DevBufs {
+    const PointConst *pts;
+    StatBlock *stats;
+    unsigned char *ring;             // records, rec_bytes apart
+    unsigned long long *ring_count;  // accepted so far (may exceed capacity)
+    RefineItem *refine;              // guard-band proposals of the current run
+    uint32_t *counters;              // [0] chunk counter, [1] refine count
+    uint32_t *status;                // bit flags (kStatus*)
+    unsigned long long ring_cap;
+    uint32_t rec_bytes;
+    uint32_t refine_cap;
+};
+
+constexpr uint32_t kStatusRefineOverflow = 1u;
+constexpr uint32_t kStatusDeadline = 2u;
+constexpr uint32_t kStatusMbarTimeout = 4u;
+constexpr uint32_t kStatusBadArg = 8u;
+
+// Arguments of one run (passed by value; the graph updates them per run).
+struct RunArgs {
+    unsigned long long idx0[kMaxPoints];
+    unsigned long long count[kMaxPoints];
+    uint32_t chunk_prefix[kMaxPoints + 1];  // cumulative chunk counts
+    uint32_t chunk;                          // proposals per chunk
+    int n_points;
+    unsigned long long deadline_ns;          // 0: none; else per-CTA budget in ns
+};
+
+// Kernel table of one KMAX instantiation of the triad sampler.
+struct TriadKernels {
+    const void *main[2][2];  // [uniform][threads: 0 -> 128, 1 -> 256]
+    const void *refine[2];
+    const void *replay[2];
+};
+void triad_kernels_k4(TriadKernels *t);
+void triad_kernels_k8(TriadKernels *t);
+void triad_kernels_k16(TriadKernels *t);
+void triad_kernels_k32(TriadKernels *t);
+void triad_kernels_k64(TriadKernels *t);
+
+inline size_t record_bytes(int K) {
+    size_t b = 32 + 8 * (size_t)K;
+    return (b + 15) & ~(size_t)15;
+}
+
+}  // namespace tkdv

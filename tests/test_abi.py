@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol that
+include/*.h declares, and its host-side precompute agrees with the oracle."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        src = re.sub(r"typedef\s+struct\s*\{.*?\}\s*\w+\s*;", " ", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\([^;{]*\)\s*;",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libtkdv():
+    from paper_2411_16952_gb300 import _build
+    if not os.path.exists(_build.LIB) or os.path.getmtime(_build.LIB) < _build._deps_mtime():
+        try:
+            _build.nvcc()
+        except RuntimeError:
+            pytest.skip("no nvcc to build libtkdv.so")
+        _build.build()
+    return C.CDLL(_build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("sampler_create", "sampler_create_ex", "sampler_run", "sampler_stats", "sampler_samples",
+              "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libtkdv):
+    missing = [n for n in declared_functions() if not hasattr(libtkdv, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_header():
+    import paper_2411_16952_gb300 as T
+    for n in declared_functions():
+        assert hasattr(T, n), n
+
+
+def test_create_without_gpu_fails_loudly(libtkdv):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2411_16952_gb300 as T
+    with pytest.raises(T.TkdvError) as ei:
+        T.sampler_create(16, 20.0, 1.0, 75.0, T.PROPOSAL_PAPER)
+    assert ei.value.code == -3  # TKDV_ERR_CUDA: no device, no CPU fallback
+
+
+def test_invalid_arguments_are_rejected(libtkdv):
+    import paper_2411_16952_gb300 as T
+    for args, code in [((0, 20.0, 1.0, 0.0, 1), -1), ((65, 20.0, 1.0, 0.0, 1), -1),
+                       ((16, -1.0, 1.0, 0.0, 1), -1), ((16, 20.0, 0.0, 0.0, 1), -1),
+                       ((16, 20.0, 1.0, 0.0, 7), -1), ((16, 1e4, 1.0, 0.0, 1), -2)]:
+        with pytest.raises(T.TkdvError) as ei:
+            T.sampler_create(*args)
+        assert ei.value.code == code, args
+
+
+@pytest.mark.parametrize("K,bp", [(1, 0.5), (2, 3.0), (8, 30.0), (16, 20.0), (32, 20.0), (32, 60.0),
+                                  (64, 40.0), (16, 0.0)])
+def test_library_alpha_star_matches_oracle(libtkdv, K, bp):
+    import paper_2411_16952_gb300 as T
+    assert abs(T.tkdv_alpha_star(K, bp) - O.alpha_star(K, bp)) < 1e-13
+
+
+@pytest.mark.parametrize("K,E0,bp,r,prop", [(2, 1.0, 3.0, 40.0, O.PAPER), (2, 1.0, 3.0, 40.0, O.UNIFORM),
+                                             (16, 1.0, 20.0, 0.0, O.PAPER), (16, 1.0, 20.0, 75.0, O.PAPER),
+                                             (16, 1.0, 20.0, 75.0, O.UNIFORM),
+                                             (16, 1.7, 40.0, 30.0, O.PAPER), (8, 0.6, 12.0, 200.0, O.PAPER)])
+def test_library_envelope_matches_oracle(libtkdv, K, E0, bp, r, prop):
+    """Two independent optimisers (oracle: Nelder-Mead; library: L-BFGS with the
+    analytic gradient) reach the same maximum of log f/g."""
+    import paper_2411_16952_gb300 as T
+    pt = O.make_point(K, E0, bp, r, prop)
+    lm_o = O.log_M(pt, 4)
+    s2 = np.array(pt.sigma2[:K]) if prop == O.PAPER else None
+    lm_l = T.tkdv_log_M(K, bp, E0, r, s2)
+    assert abs(lm_l - lm_o) < 1e-8 * (1 + abs(lm_o)), (lm_l, lm_o)
