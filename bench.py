@@ -85,7 +85,7 @@ class Clocks:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(rows), "reasons": reasons}
 
@@ -221,7 +221,8 @@ def main():
     peaks, peak_src = measured_peaks()
     wl, pts = workload_points(rank, args.n_per_point)
     K, E0, n = wl["K"], wl["E0"], args.n_per_point
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     points = [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=pid) for bp, r, pid in pts]
     S = T.Sampler(K, points, sample_capacity=1 << 21, stream=stream)
     if not args.no_autotune:

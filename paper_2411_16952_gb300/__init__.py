@@ -286,7 +286,12 @@ class Sampler:
         o = tkdv_options()
         o.K, o.h3_mode, o.grid_N = K, h3_mode, grid_N
         o.sample_capacity = sample_capacity
-        o.cuda_stream = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        if stream is None:
+            o.cuda_stream = None  # the library makes its own stream
+        else:
+            handle = int(getattr(stream, "cuda_stream", stream))
+            # handle 0 is the legacy default stream; pass cudaStreamLegacy (0x1) for it
+            o.cuda_stream = C.c_void_p(handle if handle != 0 else 1)
         o.use_graph = 1 if use_graph else 0
         o.ctas_per_sm, o.threads_per_cta = ctas_per_sm, threads_per_cta
         self.h = sampler_create_ex(points, o)
