@@ -55,7 +55,7 @@ def alg_ops_per_proposal(K: int) -> int:
 
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -68,7 +68,9 @@ class Clocks:
         except OSError:
             self.p = None
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Median SM clock and the throttle reasons seen between the wall-clock
+        times t_begin and t_end (datetime; all samples when not given)."""
         if self.p is None:
             return None
         self.p.terminate()
@@ -80,6 +82,17 @@ class Clocks:
         self.f.seek(0)
         rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
         os.unlink(self.f.name)
+        if t_begin is not None:
+            import datetime as dt
+            kept = []
+            for r in rows:
+                try:
+                    ts = dt.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    continue
+                if t_begin <= ts <= t_end:
+                    kept.append(r)
+            rows = kept or rows
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -229,6 +242,8 @@ def main():
         S.autotune(1 << 22)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
+    import datetime as dt
+    clk = Clocks(local)  # started before the warm-up so that its start-up stays out of the timed steps
     seed = 0
     for _ in range(args.warmup):
         S.run(n, seed)
@@ -237,7 +252,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = Clocks(local)
+    t_begin = dt.datetime.now()
     evs = []
     for _ in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the step events)
@@ -247,7 +262,7 @@ def main():
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    clocks = clk.stop(t_begin, dt.datetime.now())
     step_ms = [a.elapsed_time(b) for a, b in evs]
     st = S.stats()
     acc = sum(s["n_accepted"] for s in st)
