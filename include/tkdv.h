@@ -54,6 +54,7 @@ extern "C" {
 #define TKDV_ERR_TIMEOUT (-5)     /* a device wait hit its iteration limit; results of that run are void */
 #define TKDV_ERR_UNSUPPORTED (-6) /* requested form not available on this device */
 #define TKDV_ERR_ENVELOPE (-7)    /* envelope search failed (non-finite log M) */
+#define TKDV_ERR_TOO_LARGE (-8)   /* sampler_run_static: more proposals than its fixed scratch holds */
 
 /* ---- proposal kinds (Sec. III) ------------------------------------------ */
 #define TKDV_PROPOSAL_UNIFORM 0 /* uniform measure mu0 on the sphere (Eq. 15); the naive baseline */
@@ -204,6 +205,40 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
 
 /* sampler_launch_config: the launch shape of the next run. */
 int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk);
+
+/* ---- one run without any allocation --------------------------------------
+   sampler_run_static: the paper has no counterpart; this is a service for
+   callers that cannot allocate device memory: code whose device memory is
+   owned by another allocator (a framework that reserved the whole pool up
+   front), latency-critical loops where cudaMalloc/cudaFree would synchronise
+   the device, and plugin hosts that forbid device allocation.
+
+   It runs proposals idx0 .. idx0 + n_proposals - 1 of one point with the same
+   kernels as sampler_run_ranges() and calls no cudaMalloc, cudaFree or other
+   allocating routine.  Its scratch (the point table, statistics, counters and
+   the FP64 guard-band queue, about 4 MiB) is a fixed array inside this
+   library that every GPU which loads the library holds until the process
+   exits.  The first call on a device looks up that array's device address
+   (cudaGetSymbolAddress, once per device); make that first call before any
+   stream capture.  Every call shares the array: each call clears it first,
+   and calls whose work overlaps on the GPU (other host threads, other
+   streams) race on it and must not be issued.
+     K           modes, 1..64
+     point       host struct; override_logM must be 1 with the envelope in
+                 logM (tkdv_log_M computes it), else TKDV_ERR_INVALID_ARG
+     n_proposals at most TKDV_STATIC_MAX_PROPOSALS, else TKDV_ERR_TOO_LARGE
+                 (split larger ranges over several calls with advancing idx0)
+     records     caller's DEVICE buffer of capacity records of
+                 tkdv_record_bytes(K) bytes (may be NULL with capacity 0)
+     n_records   host; records written (<= capacity), may be NULL
+     stats       host; statistics of this call alone, may be NULL
+     cuda_stream stream to run on (NULL: the legacy default stream)
+   The call returns after the run has finished.  Errors: INVALID_ARG,
+   NO_ALPHA, TOO_LARGE, CUDA, TIMEOUT. */
+#define TKDV_STATIC_MAX_PROPOSALS 262144
+int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0, uint64_t n_proposals, uint64_t seed,
+                       void *records, uint64_t capacity, uint64_t *n_records, tkdv_stats *stats,
+                       void *cuda_stream);
 
 const char *sampler_last_error(const tkdv_sampler *h);
 void sampler_destroy(tkdv_sampler *h);

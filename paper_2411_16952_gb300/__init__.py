@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(HERE, "libtkdv.so")
 
 TKDV_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "NO_ALPHA", -3: "CUDA", -4: "OOM", -5: "TIMEOUT",
-          -6: "UNSUPPORTED", -7: "ENVELOPE"}
+          -6: "UNSUPPORTED", -7: "ENVELOPE", -8: "TOO_LARGE"}
+STATIC_MAX_PROPOSALS = 262144
 PROPOSAL_UNIFORM, PROPOSAL_PAPER, PROPOSAL_LEARNED = 0, 1, 2
 H3_TRIAD_F32, H3_GRID_BF16X3 = 0, 1
 MAX_POINTS = 64
@@ -34,7 +35,7 @@ EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler
             "sampler_run_budgets", "sampler_run_ranges", "sampler_stats", "sampler_samples",
             "sampler_reset", "sampler_sync", "sampler_set_deadline_ns", "sampler_point_info",
             "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
-            "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M"]
+            "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static"]
 
 
 class TkdvError(RuntimeError):
@@ -103,6 +104,8 @@ def lib():
             L.sampler_destroy.restype = None
             L.tkdv_alpha_star.argtypes = [i, d, dp]
             L.tkdv_log_M.argtypes = [i, d, d, d, dp, dp]
+            L.sampler_run_static.argtypes = [i, C.POINTER(tkdv_point), u64, u64, u64, vp, u64, u64p,
+                                             C.POINTER(tkdv_stats), vp]
             _lib = L
     return _lib
 
@@ -236,6 +239,22 @@ def sampler_last_error(h=None):
 def sampler_destroy(h):
     if h:
         lib().sampler_destroy(h)
+
+
+def sampler_run_static(K, point, idx0, n_proposals, seed, records=None, capacity=0, stream=None):
+    """One run that allocates nothing (see include/tkdv.h): for callers whose
+    device memory is owned elsewhere or who must not call cudaMalloc.
+    records: the caller's torch uint8 CUDA tensor of capacity records (or None).
+    Returns (stats dict, number of records written)."""
+    st = tkdv_stats()
+    nrec = C.c_uint64()
+    dst = C.c_void_p(records.data_ptr()) if records is not None else None
+    s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)) or 1)
+    rc = lib().sampler_run_static(K, C.byref(point), idx0, n_proposals, seed, dst,
+                                  capacity if records is not None else 0, C.byref(nrec), C.byref(st), s)
+    if rc != TKDV_OK:
+        raise TkdvError(rc, "sampler_run_static")
+    return _stats_dict(st), int(nrec.value)
 
 
 # ---- helpers ---------------------------------------------------------------
