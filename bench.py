@@ -41,16 +41,30 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def alg_ops_per_proposal(K: int) -> int:
-    """Ideal thread-instruction count of one proposal of the FP32 triad form:
-    Philox4x32-10 (ceil(K/2)+1 blocks x 10 rounds x 4: two wide multiplies and
-    two 3-input xors), Box-Muller and scaling (20 per mode), the |x|^2, S, Q,
-    u0 accumulations (4 per mode), the symmetric double sum of Eq. (42)
-    (4 FMA per pair k < n-k, 3 for the middle term, 4 for the outer update),
-    and 40 for log Q, ln U, the ratio and the decision."""
+def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
+    """Ideal thread-instruction count of one proposal.
+
+    Both forms: Philox4x32-10 (ceil(K/2)+1 blocks x 10 rounds x 4: two wide
+    multiplies and two 3-input xors), Box-Muller and sigma scaling (20 per
+    mode), the |x|^2, S, Q, u0 accumulations (4 per mode), 40 for log Q, ln U,
+    the ratio and the decision.
+    triad: the symmetric double sum of Eq. (42) (4 FMA per pair k < n-k, 3 for
+    the middle term, 4 for the outer update).
+    grid: BF16 hi/lo split and shared-memory store of the 2K values (3.5 per
+    value), the cube-and-sum of the N grid values (2 per value) and their
+    TMEM loads (1 per 32)."""
     blocks = (K + 1) // 2 + 1
+    common = 40 * blocks + 20 * K + 4 * K + 40
+    if form == "grid":
+        return int(common + 3.5 * 2 * K + 2 * grid_N + grid_N // 32)
     triad = sum(4 * ((n - 1) // 2) + (3 if n % 2 == 0 else 0) + 4 for n in range(2, K + 1))
-    return 40 * blocks + 20 * K + 4 * K + triad + 40
+    return common + triad
+
+
+def tensor_flops_per_proposal(K: int, grid_N: int) -> int:
+    """Three BF16 products of a 2K-padded-to-64 row with the 2K x N basis."""
+    ka = (2 * K + 63) // 64 * 64
+    return 3 * 2 * ka * grid_N
 
 
 class Clocks:
@@ -216,6 +230,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-proposals", type=int, default=1 << 22)
     ap.add_argument("--ref-exact-envelope", action="store_true")
+    ap.add_argument("--forms", default="", help="comma list of forms to time (default: all)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.impl == "reference":
@@ -233,90 +248,113 @@ def main():
     _build.build()
     peaks, peak_src = measured_peaks()
     wl, pts = workload_points(rank, args.n_per_point)
-    K, E0, n = wl["K"], wl["E0"], args.n_per_point
+    K, E0, n, gN = wl["K"], wl["E0"], args.n_per_point, wl["grid_N"]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    points = [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=pid) for bp, r, pid in pts]
-    S = T.Sampler(K, points, sample_capacity=1 << 21, stream=stream)
-    if not args.no_autotune:
-        S.autotune(1 << 22)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
     import datetime as dt
-    clk = Clocks(local)  # started before the warm-up so that its start-up stays out of the timed steps
-    seed = 0
-    for _ in range(args.warmup):
-        S.run(n, seed)
-    S.sync()
-    S.reset()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_begin = dt.datetime.now()
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the step events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        S.run(n, seed)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
-    clocks = clk.stop(t_begin, dt.datetime.now())
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    st = S.stats()
-    acc = sum(s["n_accepted"] for s in st)
-    prop = sum(s["n_proposals"] for s in st)
-    t_s = sum(step_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        cnt = torch.tensor([acc, prop], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(cnt)
-        t_s, acc, prop = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
-    launch = S.launch_config()
-
-    # ---- end to end through the public API with host buffers ------------
-    S.reset()
-    rec_bytes = T.tkdv_record_bytes(K)
-    host_rec = np.zeros(1 << 21 * 1, dtype=np.uint8)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d2h = 0
-    e2e_acc = 0
-    for i in range(args.steps):
+    clk = Clocks(local)  # started before any warm-up so that its start-up stays out of the timed steps
+    forms = {"triad_f32_paper": (T.H3_TRIAD_F32, T.PROPOSAL_PAPER),
+             "grid_bf16x3_paper": (T.H3_GRID_BF16X3, T.PROPOSAL_PAPER)}
+    if args.forms:
+        forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
+    headline = "grid_bf16x3_paper" if "grid_bf16x3_paper" in forms else next(iter(forms))
+    results = {}
+    windows = []
+    for fname, (mode, prop) in forms.items():
+        points = [T.make_point(bp, E0, r, prop, point_id=pid) for bp, r, pid in pts]
+        S = T.Sampler(K, points, h3_mode=mode, grid_N=gN if mode == T.H3_GRID_BF16X3 else 0,
+                      sample_capacity=1 << 21, stream=stream)
+        if not args.no_autotune:
+            S.autotune(1 << 22)
+        seed = 0
+        for _ in range(args.warmup):
+            S.run(n, seed)
+        S.sync()
         S.reset()
-        S.run(n, seed + 1 + i)
-        sts = S.stats()
-        recs = S.samples(1 << 21)
-        e2e_acc += sum(s["n_accepted"] for s in sts)
-        d2h += len(recs["idx"]) * rec_bytes + len(sts) * 2304
-    e2e_t = time.perf_counter() - t0
-    S.close()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_begin = dt.datetime.now()
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the step events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.run(n, seed)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        windows.append((t_begin, dt.datetime.now()))
+        step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+        st = S.stats()
+        acc = sum(s["n_accepted"] for s in st)
+        prop_n = sum(s["n_proposals"] for s in st)
+        refined = sum(s["n_refined"] for s in st)
+        t_s = sum(step_ms) / 1e3
+        if ws > 1:
+            tt = torch.tensor([t_s], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            cnt = torch.tensor([acc, prop_n], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(cnt)
+            t_s, acc, prop_n = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
+        res = {"accepted_per_s": acc / t_s, "proposals_per_s": prop_n / t_s, "ms_per_step": 1e3 * t_s / args.steps,
+               "acceptance": acc / max(prop_n, 1), "refined_fraction": refined / max(prop_n, 1),
+               "launch": S.launch_config()}
+        if fname == headline:
+            # end to end through the public API with host buffers: run, then
+            # statistics and accepted records copied to the host every step
+            S.reset()
+            rec_bytes = T.tkdv_record_bytes(K)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d2h = 0
+            e2e_acc = 0
+            for i in range(args.steps):
+                S.reset()
+                S.run(n, seed + 1 + i)
+                sts = S.stats()
+                recs = S.samples(1 << 21)
+                e2e_acc += sum(s["n_accepted"] for s in sts)
+                d2h += len(recs["idx"]) * rec_bytes + len(sts) * 2304
+            e2e_t = time.perf_counter() - t0
+            res["e2e"] = {"value": e2e_acc / e2e_t, "unit": "accepted samples/s",
+                          "h2d_bytes_per_step": 8 * 2 * len(pts) + 8, "d2h_bytes_per_step": d2h // args.steps}
+        S.close()
+        results[fname] = res
+    clocks = clk.stop(windows[0][0], windows[-1][1])
 
-    ops = alg_ops_per_proposal(K)
-    step_s = t_s / args.steps
-    achieved = ops * (prop / args.steps) / step_s / 1e12
+    h = results[headline]
+    form_kind = "grid" if headline.startswith("grid") else "triad"
+    ops = alg_ops_per_proposal(K, form_kind, gN)
+    step_s = h["ms_per_step"] / 1e3
+    props_per_step = h["proposals_per_s"] * step_s
+    achieved = ops * props_per_step / step_s / 1e12
     peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": None, "ops_per_proposal": ops, "kernel": "k_sample_%s" % form_kind,
+            "note": "ideal thread-instruction count per proposal (bench.py alg_ops_per_proposal); peak = "
+                    "152 SM x 128 lanes x max SM clock (%s sm_max_mhz)" % peak_src}
+    if form_kind == "grid":
+        tf = tensor_flops_per_proposal(K, gN) * h["proposals_per_s"] / 1e12
+        roof["tensor"] = {"achieved_tflops": tf, "peak_tflops": float(peaks.get("bf16_tflops_sustained", 1735.3)),
+                          "frac": tf / float(peaks.get("bf16_tflops_sustained", 1735.3)),
+                          "note": "BF16 hi/lo x3 contraction flops of the whole sampler run over its duration, "
+                                  "against the sustained cuBLAS BF16 peak (%s)" % peak_src}
     line = {
-        "metric": METRIC, "value": acc / t_s, "unit": "accepted samples/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "proposals_per_s": prop / t_s,
-        "acceptance": acc / max(prop, 1),
-        "forms": {"triad_f32_paper": {"accepted_per_s": acc / t_s, "proposals_per_s": prop / t_s}},
-        "config": {"workload": wl["name"], "K": K, "grid_N": wl["grid_N"], "points": len(pts),
-                   "proposals_per_point_per_step": n, "form": "triad_f32", "proposal": "paper",
+        "metric": METRIC, "value": h["accepted_per_s"], "unit": "accepted samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32" if form_kind == "grid" else "f32", "data": "synthetic",
+        "proposals_per_s": h["proposals_per_s"], "acceptance": h["acceptance"],
+        "headline_form": headline, "forms": results,
+        "config": {"workload": wl["name"], "K": K, "grid_N": gN, "points": len(pts),
+                   "proposals_per_point_per_step": n, "proposal": "paper",
                    "l2": "256 MiB buffer written between timed steps, outside the step events",
-                   "launch": launch, "parallelism": "points x index ranges, weak per GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "ops_per_proposal": ops,
-                     "note": "ideal thread-instruction count per proposal; peak = 152 SM x 128 lanes x "
-                             "max SM clock (%s sm_max_mhz)" % peak_src},
-        "e2e": {"value": e2e_acc / e2e_t, "unit": "accepted samples/s",
-                "h2d_bytes_per_step": 8 * 2 * len(pts) + 8, "d2h_bytes_per_step": d2h // args.steps},
-        "gpu_launches": 2 * args.steps,
+                   "parallelism": "points x index ranges, weak per GPU"},
+        "roofline": roof,
+        "e2e": h.get("e2e"),
+        "gpu_launches": 2 * args.steps * len(forms),
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

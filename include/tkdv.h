@@ -88,7 +88,8 @@ typedef struct {
 typedef struct {
     int K;                    /* modes, 1..64, common to all points of the handle */
     int h3_mode;              /* TKDV_H3_* */
-    int grid_N;               /* grid points for TKDV_H3_GRID_BF16X3: multiple of 16, > 3K, <= 256 */
+    int grid_N;               /* grid points for TKDV_H3_GRID_BF16X3: multiple of 32, > 3K, <= 256;
+                                 0: the smallest such (128 for K = 32) */
     uint64_t sample_capacity; /* accepted records kept per handle (ring; excess is counted, not kept) */
     void *cuda_stream;        /* cudaStream_t to launch on; NULL: the handle makes its own */
     int use_graph;            /* 1: launch each run as one CUDA graph (default), 0: plain launches */
@@ -144,7 +145,10 @@ int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv
 
 /* sampler_create_ex: n_points (1..64) points sharing opt->K and opt->h3_mode,
    run together by one persistent launch (batched form).  Errors as above,
-   plus UNSUPPORTED for the grid form on a device without tcgen05. */
+   plus UNSUPPORTED for the grid form on a device without tcgen05.  The grid
+   form runs K <= 16 and K <= 32 with two 128-proposal tiles per CTA and
+   K <= 64 with one (shared memory: 2 x grid_N x 128 x 2 B basis plus 64 KB
+   per tile, 2x for K > 32). */
 int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options *opt,
                       tkdv_sampler **out);
 
@@ -185,6 +189,14 @@ int sampler_sync(tkdv_sampler *h);
    once (the flag is cleared when reported).  Statistics hold the proposals
    that did run. */
 int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns);
+
+/* sampler_set_trace: grid form only (tcgen05 contraction).  Later runs write,
+   for each of point 0's first n proposals of the run (index idx0[0] + i),
+   the pair (log f/(Mg), T) as two floats at dev_buf[2i], where
+   H3 = 2 pi (E0/2pi)^{3/2} T (Eq. 42 in these units).  dev_buf is the
+   caller's device buffer of 2n floats; n = 0 switches the trace off.
+   Errors: INVALID_ARG, UNSUPPORTED (triad form). */
+int sampler_set_trace(tkdv_sampler *h, void *dev_buf, uint64_t n);
 
 /* sampler_point_info: alpha*, log M and the K proposal variances sigma_k^2
    (Eq. 25, or the learned ones) of point p; any output may be NULL. */
@@ -242,6 +254,55 @@ int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0, uint64_t n
 
 const char *sampler_last_error(const tkdv_sampler *h);
 void sampler_destroy(tkdv_sampler *h);
+
+/* ---- learned proposal ------------------------------------------------------
+   Not in the paper.  A 4 -> 64 -> 64 -> 64 MLP (tanh hidden layers, linear
+   output) maps the features of a parameter point (tkdv_mlp_features) to
+   per-mode log-variance corrections c_k of the paper's proposal:
+   sigma_k'^2 = sigma_k^2 (Eq. 25) * e^{c_k}, c gauge-fixed to mean zero over
+   k = 1..K (the proposal density is unchanged by a common factor).  The
+   proposal stays a projected centred Gaussian, so its density keeps the closed
+   form of Eqs. (33)-(38) and the accept test stays exact (pass c as
+   tkdv_point.log_var_correction; the envelope is recomputed for it).
+   Training minimises, per point over accepted samples i (draws from f),
+     J_tau = tau log mean_i exp((z_i + ell_i)/tau),  ell_i = -log g(xh_i)
+           = K ln Q_i - sum_k ln w'_k,  z_i = -beta H_i;
+   tau <= 0 means the plain mean (KL(f || g) up to a constant).  Parameters:
+   FP32 masters updated by Adam, used as BF16 copies; FP32 accumulation.
+   Parameter layout (TKDV_MLP_NPARAM floats): W1[64][4], b1[64], W2[64][64],
+   b2[64], W3[64][64], b3[64] (row = output unit).  All calls synchronise. */
+#define TKDV_MLP_NPARAM 8640
+typedef struct tkdv_mlp tkdv_mlp;
+/* hidden layers seeded normal, output layer zero (c = 0: the paper proposal) */
+int tkdv_mlp_create(uint64_t seed, tkdv_mlp **out);
+void tkdv_mlp_destroy(tkdv_mlp *m);
+const char *tkdv_mlp_last_error(const tkdv_mlp *m);
+/* out4 = [ln beta'/ln 100, ln E0, ln(1 + beta' C3/C2 / 100)/ln 100, K/64] */
+int tkdv_mlp_features(int K, double beta_p, double E0, double r, double *out4);
+/* FP32 masters and/or the BF16 values in use (as floats), host arrays of NPARAM */
+int tkdv_mlp_get_params(tkdv_mlp *m, float *master, float *bf16_values);
+/* replaces the masters (BF16 copies refreshed), resets Adam */
+int tkdv_mlp_set_params(tkdv_mlp *m, const float *master);
+/* c_out (P x 64, host): gauge-fixed corrections for P feature rows (P x 4) */
+int tkdv_mlp_infer(tkdv_mlp *m, int P, const double *feats, const int *K, double *c_out);
+/* training set from host arrays: per point K, features (P x 4), paper weights
+   w_k = 1/sigma_k^2 (P x 64), counts[p] rows; s_rows holds sum(counts) rows of
+   round_up(max K, 4) floats (s_k = xh_k^2 + xh_{K+k}^2, zero padded), point
+   after point; z (sum(counts) floats, may be NULL: zeros) = -beta H */
+int tkdv_mlp_set_data(tkdv_mlp *m, int P, const int *K, const double *feats, const double *w_paper,
+                      const uint64_t *counts, const float *s_rows, const float *z);
+/* training set from a DEVICE buffer of n_records sampler records
+   (tkdv_record layout, K_records modes): record point p -> training point p,
+   at most max_per_point rows each; zcoef[2p] = beta'/(E0 K^2), zcoef[2p+1] = C3/C2 */
+int tkdv_mlp_set_data_records(tkdv_mlp *m, int P, const int *K, const double *feats, const double *w_paper,
+                              const double *zcoef, const void *records_dev, uint64_t n_records, int K_records,
+                              uint64_t max_per_point);
+/* rows per point of the current training set */
+int tkdv_mlp_rows(tkdv_mlp *m, uint64_t *counts);
+/* one pass: forward, loss, backward (grad_out: NPARAM floats, may be NULL),
+   and an Adam update with learning rate lr when update != 0; *loss = sum over
+   points of J (before the update) */
+int tkdv_mlp_step(tkdv_mlp *m, float lr, float tau, int update, double *loss, float *grad_out);
 
 /* ---- host precompute, exported for tests --------------------------------- */
 /* alpha* = root of F(alpha) = 1 - (alpha/K) sum_k 1/(1 + alpha beta' k^2/K^3)

@@ -35,7 +35,11 @@ EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler
             "sampler_run_budgets", "sampler_run_ranges", "sampler_stats", "sampler_samples",
             "sampler_reset", "sampler_sync", "sampler_set_deadline_ns", "sampler_point_info",
             "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
-            "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static"]
+            "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static",
+            "sampler_set_trace", "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
+            "tkdv_mlp_features", "tkdv_mlp_get_params", "tkdv_mlp_set_params", "tkdv_mlp_infer",
+            "tkdv_mlp_set_data", "tkdv_mlp_set_data_records", "tkdv_mlp_rows", "tkdv_mlp_step"]
+MLP_NPARAM = 8640
 
 
 class TkdvError(RuntimeError):
@@ -94,6 +98,21 @@ def lib():
             L.sampler_reset.argtypes = [vp]
             L.sampler_sync.argtypes = [vp]
             L.sampler_set_deadline_ns.argtypes = [vp, u64]
+            L.sampler_set_trace.argtypes = [vp, vp, u64]
+            fp, ip = C.POINTER(C.c_float), C.POINTER(C.c_int)
+            L.tkdv_mlp_create.argtypes = [u64, C.POINTER(vp)]
+            L.tkdv_mlp_destroy.argtypes = [vp]
+            L.tkdv_mlp_destroy.restype = None
+            L.tkdv_mlp_last_error.argtypes = [vp]
+            L.tkdv_mlp_last_error.restype = C.c_char_p
+            L.tkdv_mlp_features.argtypes = [i, d, d, d, dp]
+            L.tkdv_mlp_get_params.argtypes = [vp, fp, fp]
+            L.tkdv_mlp_set_params.argtypes = [vp, fp]
+            L.tkdv_mlp_infer.argtypes = [vp, i, dp, ip, dp]
+            L.tkdv_mlp_set_data.argtypes = [vp, i, ip, dp, dp, u64p, fp, fp]
+            L.tkdv_mlp_set_data_records.argtypes = [vp, i, ip, dp, dp, dp, vp, u64, i, u64]
+            L.tkdv_mlp_rows.argtypes = [vp, u64p]
+            L.tkdv_mlp_step.argtypes = [vp, C.c_float, C.c_float, i, dp, fp]
             L.sampler_point_info.argtypes = [vp, i, dp, dp, dp]
             L.sampler_replay.argtypes = [vp, i, u64p, u64, u64, dp]
             L.sampler_autotune.argtypes = [vp, u64, dp]
@@ -195,6 +214,13 @@ def sampler_sync(h):
     _check(lib().sampler_sync(h), h)
 
 
+def sampler_set_trace(h, dev_tensor, n):
+    """Grid form: later runs write (log f/(Mg), T) of point 0's first n proposals
+    into dev_tensor (a float32 CUDA tensor of 2n elements, or None to stop)."""
+    ptr = C.c_void_p(dev_tensor.data_ptr()) if dev_tensor is not None else None
+    _check(lib().sampler_set_trace(h, ptr, n if dev_tensor is not None else 0), h)
+
+
 def sampler_set_deadline_ns(h, ns):
     _check(lib().sampler_set_deadline_ns(h, ns), h)
 
@@ -255,6 +281,115 @@ def sampler_run_static(K, point, idx0, n_proposals, seed, records=None, capacity
     if rc != TKDV_OK:
         raise TkdvError(rc, "sampler_run_static")
     return _stats_dict(st), int(nrec.value)
+
+
+# ---- learned proposal ------------------------------------------------------
+def _mcheck(rc, m):
+    if rc != TKDV_OK:
+        msg = lib().tkdv_mlp_last_error(m)
+        raise TkdvError(rc, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def tkdv_mlp_create(seed=0):
+    m = C.c_void_p()
+    _check(lib().tkdv_mlp_create(seed, C.byref(m)))
+    return m
+
+
+def tkdv_mlp_destroy(m):
+    if m:
+        lib().tkdv_mlp_destroy(m)
+
+
+def tkdv_mlp_last_error(m):
+    s = lib().tkdv_mlp_last_error(m)
+    return s.decode() if s else ""
+
+
+def tkdv_mlp_features(K, beta_p, E0, r):
+    out = np.zeros(4)
+    _check(lib().tkdv_mlp_features(K, beta_p, E0, r, _dptr(out)))
+    return out
+
+
+def tkdv_mlp_get_params(m):
+    master = np.zeros(MLP_NPARAM, dtype=np.float32)
+    bf = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _mcheck(lib().tkdv_mlp_get_params(m, _fptr(master), _fptr(bf)), m)
+    return master, bf
+
+
+def tkdv_mlp_set_params(m, master):
+    a = np.ascontiguousarray(np.asarray(master, dtype=np.float32))
+    assert a.size == MLP_NPARAM
+    _mcheck(lib().tkdv_mlp_set_params(m, _fptr(a)), m)
+
+
+def tkdv_mlp_infer(m, feats, Ks):
+    f = np.ascontiguousarray(np.asarray(feats, dtype=np.float64).reshape(-1, 4))
+    P = f.shape[0]
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    out = np.zeros((P, 64))
+    _mcheck(lib().tkdv_mlp_infer(m, P, _dptr(f), k.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out)), m)
+    return out
+
+
+def tkdv_mlp_set_data(m, Ks, feats, w_paper, s_list, z_list=None):
+    """Training set from host arrays: s_list[p] is (n_p, K_p) pair energies."""
+    P = len(Ks)
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    f = np.ascontiguousarray(np.asarray(feats, dtype=np.float64).reshape(P, 4))
+    wp = np.zeros((P, 64))
+    for p in range(P):
+        wp[p, :Ks[p]] = w_paper[p]
+    stride = (max(Ks) + 3) // 4 * 4
+    counts = np.array([len(s) for s in s_list], dtype=np.uint64)
+    rows = np.zeros((int(counts.sum()), stride), dtype=np.float32)
+    z = np.zeros(int(counts.sum()), dtype=np.float32)
+    o = 0
+    for p in range(P):
+        n = len(s_list[p])
+        rows[o:o + n, :Ks[p]] = s_list[p]
+        if z_list is not None:
+            z[o:o + n] = z_list[p]
+        o += n
+    _mcheck(lib().tkdv_mlp_set_data(m, P, k.ctypes.data_as(C.POINTER(C.c_int)), _dptr(f), _dptr(wp),
+                                    counts.ctypes.data_as(C.POINTER(C.c_uint64)), _fptr(rows), _fptr(z)), m)
+
+
+def tkdv_mlp_set_data_records(m, Ks, feats, w_paper, zcoef, records_dev, n_records, K_records, max_per_point):
+    P = len(Ks)
+    k = np.ascontiguousarray(np.asarray(Ks, dtype=np.int32))
+    f = np.ascontiguousarray(np.asarray(feats, dtype=np.float64).reshape(P, 4))
+    wp = np.zeros((P, 64))
+    for p in range(P):
+        wp[p, :Ks[p]] = w_paper[p]
+    zc = np.ascontiguousarray(np.asarray(zcoef, dtype=np.float64).reshape(P, 2))
+    _mcheck(lib().tkdv_mlp_set_data_records(m, P, k.ctypes.data_as(C.POINTER(C.c_int)), _dptr(f), _dptr(wp),
+                                            _dptr(zc), C.c_void_p(records_dev.data_ptr()), n_records,
+                                            K_records, max_per_point), m)
+
+
+def tkdv_mlp_rows(m, P):
+    c = np.zeros(P, dtype=np.uint64)
+    _mcheck(lib().tkdv_mlp_rows(m, c.ctypes.data_as(C.POINTER(C.c_uint64))), m)
+    return c
+
+
+def tkdv_mlp_step(m, lr=1e-2, tau=0.0, update=True, want_grad=False):
+    loss = C.c_double()
+    g = np.zeros(MLP_NPARAM, dtype=np.float32) if want_grad else None
+    _mcheck(lib().tkdv_mlp_step(m, lr, tau, 1 if update else 0, C.byref(loss),
+                                _fptr(g) if want_grad else None), m)
+    return (loss.value, g) if want_grad else loss.value
 
 
 # ---- helpers ---------------------------------------------------------------
@@ -335,6 +470,9 @@ class Sampler:
 
     def sync(self):
         sampler_sync(self.h)
+
+    def set_trace(self, dev_tensor, n):
+        sampler_set_trace(self.h, dev_tensor, n)
 
     def set_deadline_ns(self, ns):
         sampler_set_deadline_ns(self.h, ns)

@@ -1,0 +1,6 @@
+// Grid-form (tensor-core) sampler kernels for up to 32 modes, double-buffered tiles.
+#include "grid_impl.cuh"
+
+namespace tkdv {
+void grid_kernels_k32(GridKernels *t) { fill_grid_kernels<32, 2>(t); }
+}  // namespace tkdv

@@ -51,6 +51,23 @@ __device__ __forceinline__ double u01d(uint32_t w) {
     return (double)((w >> 8) | 1u) * 0x1p-24;
 }
 
+// Box-Muller pair in FP32: rho = -2 ln u1 (the squared radius), and
+// (z_cos, z_sin) = sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
+// exactly to 2 pi (u2 - 1/2) in (-pi, pi), where the hardware sine/cosine have
+// an absolute error below 2^-21.4, and cos(t - pi) = -cos t, sin(t - pi) =
+// -sin t restore the signs; sqrt(rho) = rho * rsqrt(rho).  The FP32 decision
+// guard covers these errors (draws near the threshold are redone in FP64).
+__device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float &rho, float &zc, float &zs) {
+    const float u1 = u01f(w1);
+    const float u2 = u01f(w2);
+    rho = -2.f * logf(u1);
+    const float nrad = -(rho * rsqrtf(rho));
+    float sn, cs;
+    __sincosf(6.28318530717958647692f * (u2 - 0.5f), &sn, &cs);
+    zc = nrad * cs;
+    zs = nrad * sn;
+}
+
 // Order-preserving map float -> uint32 (for atomicMax on signed floats).
 __device__ __forceinline__ uint32_t fkey(float f) {
     uint32_t b = __float_as_uint(f);
@@ -117,15 +134,10 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
             if (m < KMAX) {
-                const float u1 = u01f(h ? w.z : w.x);
-                const float u2 = u01f(h ? w.w : w.y);
-                const float rho = -2.f * logf(u1);
-                const float rad = sqrtf(rho);
-                float sn, cs;
-                sincospif(2.f * u2, &sn, &cs);
+                float rho, zc, zs;
+                box_muller_f32(h ? w.z : w.x, h ? w.w : w.y, rho, zc, zs);
                 const float s = UNIF ? act[m] : sig[m];
-                const float sr = s * rad;
-                const float xm = sr * cs, ym = sr * sn;
+                const float xm = s * zc, ym = s * zs;
                 d.x[m] = xm;
                 d.y[m] = ym;
                 const float sk = (s * s) * rho;
@@ -300,8 +312,8 @@ __device__ __forceinline__ void write_record(unsigned char *rec, unsigned long l
 }
 
 // ---- the persistent sampler ----------------------------------------------
-template <int KMAX, bool UNIF, int NT>
-__global__ void __launch_bounds__(NT) k_sample_triad(DevBufs B, RunArgs A, uint32_t k0, uint32_t k1) {
+template <int KMAX, bool UNIF, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_sample_triad(DevBufs B, RunArgs A, uint32_t k0, uint32_t k1) {
     __shared__ uint32_t s_hist[kHistBins];
     __shared__ uint32_t s_exc[kExcBins];
     __shared__ unsigned long long s_q[4];
@@ -542,10 +554,12 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
 
 template <int KMAX>
 void fill_triad_kernels(TriadKernels *t) {
-    t->main[0][0] = (const void *)k_sample_triad<KMAX, false, 128>;
-    t->main[0][1] = (const void *)k_sample_triad<KMAX, false, 256>;
-    t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128>;
-    t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256>;
+    t->main[0][0] = (const void *)k_sample_triad<KMAX, false, 128, 1>;
+    t->main[0][1] = (const void *)k_sample_triad<KMAX, false, 256, 1>;
+    t->main[0][2] = (const void *)k_sample_triad<KMAX, false, 256, 2>;
+    t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128, 1>;
+    t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256, 1>;
+    t->main[1][2] = (const void *)k_sample_triad<KMAX, true, 256, 2>;
     t->refine[0] = (const void *)k_refine<KMAX, false>;
     t->refine[1] = (const void *)k_refine<KMAX, true>;
     t->replay[0] = (const void *)k_replay<KMAX, false>;

@@ -22,6 +22,7 @@ thread_local std::string g_create_error;
 struct Launch {
     int threads = 256;
     int ctas = 0;
+    int variant = 1;  // triad form: index into TriadKernels::main[][variant]
 };
 
 }  // namespace
@@ -43,6 +44,12 @@ struct tkdv_sampler {
          *d_refine = nullptr, *d_counters = nullptr, *d_status = nullptr;
     size_t rec_bytes = 0;
     TriadKernels kt{};
+    GridKernels kg{};
+    int grid_N = 0;
+    void *d_bimg = nullptr;   // grid form: BF16 hi/lo basis image
+    size_t dyn_smem = 0;      // grid form: dynamic shared memory per CTA
+    float *trace = nullptr;   // grid form: optional per-proposal trace (device)
+    unsigned long long trace_n = 0;
     Launch launch;
     unsigned long long deadline_ns = 0;
     // graph of one run: memset(counters) -> sampler -> refine
@@ -176,18 +183,47 @@ int build_point(tkdv_sampler *h, int p, std::string &msg) {
     c.guard_abs = (float)(1e-6 + gam * std::fabs(c.cQ_d));
     c.guard_rel = (float)gam;
     c.guard_h = (float)(gam * std::fabs(c.cH_d) * std::sqrt((double)K));
+    if (h->opt.h3_mode == TKDV_H3_GRID_BF16X3) {
+        // BF16 hi/lo x3: |dU_j| <= 2^-15.4 sqrt(2K) |x| per grid value, so with
+        // sum_j U_j^2 = (N/2)|x|^2 the error of T is below 2^-14.4 sqrt(2K)
+        c.guard_h += (float)(std::ldexp(1.0, -14) * std::sqrt(2.0 * K) * std::fabs(c.cH_d));
+    }
     c.point_id = q.point_id;
     c.K = K;
     h->pc[p] = c;
     return TKDV_OK;
 }
 
-int set_default_launch(tkdv_sampler *h) {
+bool is_grid(const tkdv_sampler *h) { return h->opt.h3_mode == TKDV_H3_GRID_BF16X3; }
+
+const void *main_fn(const tkdv_sampler *h, int variant) {
     const int uni = h->all_uniform ? 1 : 0;
-    const int thr = h->launch.threads;
-    const void *fn = h->kt.main[uni][thr == 128 ? 0 : 1];
+    if (is_grid(h)) return h->kg.main[uni];
+    return h->kt.main[uni][variant];
+}
+
+// TMEM columns one grid-form CTA allocates.
+int grid_tmem_cols(const tkdv_sampler *h) {
+    int c = 32;
+    while (c < h->grid_N) c <<= 1;
+    return c * h->kg.nwg;
+}
+
+// Largest number of resident CTAs per SM for the handle's form.
+int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, thr, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads,
+                                                     is_grid(h) ? h->dyn_smem : 0));
+    if (is_grid(h)) nb = std::min(nb, 512 / grid_tmem_cols(h));  // TMEM: 512 columns per SM
+    *out = nb;
+    return TKDV_OK;
+}
+
+int set_default_launch(tkdv_sampler *h) {
+    const int thr = h->launch.threads;
+    int nb = 0;
+    int rc = max_ctas_per_sm(h, h->launch.variant, thr, &nb);
+    if (rc) return rc;
     if (nb < 1) return fail(h, TKDV_ERR_CUDA, "sampler kernel does not fit on an SM");
     int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, nb) : nb;
     h->launch.ctas = per_sm * h->num_sms;
@@ -220,6 +256,8 @@ int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned l
         a.chunk_prefix[p + 1] = (uint32_t)acc;
     }
     a.deadline_ns = h->deadline_ns;
+    a.trace = h->trace;
+    a.trace_n = h->trace ? h->trace_n : 0ull;
     h->key0 = (uint32_t)seed;
     h->key1 = (uint32_t)(seed >> 32);
     return TKDV_OK;
@@ -247,12 +285,14 @@ int build_graph(tkdv_sampler *h) {
     cudaGraphNode_t n_ms;
     CK(cudaGraphAddMemsetNode(&n_ms, h->graph, nullptr, 0, &ms));
     const int uni = h->all_uniform ? 1 : 0;
-    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
+    const unsigned char *bimg = (const unsigned char *)h->d_bimg;
+    int gN = h->grid_N;
+    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
     cudaKernelNodeParams kp{};
-    kp.func = (void *)h->kt.main[uni][h->launch.threads == 128 ? 0 : 1];
+    kp.func = (void *)main_fn(h, h->launch.variant);
     kp.gridDim = dim3(h->launch.ctas);
     kp.blockDim = dim3(h->launch.threads);
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = is_grid(h) ? (unsigned)h->dyn_smem : 0;
     kp.kernelParams = margs;
     CK(cudaGraphAddKernelNode(&h->n_main, h->graph, &n_ms, 1, &kp));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -270,15 +310,19 @@ int build_graph(tkdv_sampler *h) {
 int enqueue(tkdv_sampler *h) {
     const int uni = h->all_uniform ? 1 : 0;
     if (h->opt.use_graph) {
-        if (!h->exec || h->graph_launch.ctas != h->launch.ctas || h->graph_launch.threads != h->launch.threads) {
+        if (!h->exec || h->graph_launch.ctas != h->launch.ctas || h->graph_launch.threads != h->launch.threads ||
+            h->graph_launch.variant != h->launch.variant) {
             int rc = build_graph(h);
             if (rc) return rc;
         }
-        void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
+        const unsigned char *bimg = (const unsigned char *)h->d_bimg;
+        int gN = h->grid_N;
+        void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
         cudaKernelNodeParams kp{};
-        kp.func = (void *)h->kt.main[uni][h->launch.threads == 128 ? 0 : 1];
+        kp.func = (void *)main_fn(h, h->launch.variant);
         kp.gridDim = dim3(h->launch.ctas);
         kp.blockDim = dim3(h->launch.threads);
+        kp.sharedMemBytes = is_grid(h) ? (unsigned)h->dyn_smem : 0;
         kp.kernelParams = margs;
         CK(cudaGraphExecKernelNodeSetParams(h->exec, h->n_main, &kp));
         void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -292,9 +336,11 @@ int enqueue(tkdv_sampler *h) {
         return TKDV_OK;
     }
     CK(cudaMemsetAsync(h->d_counters, 0, 8, h->stream));
-    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1};
-    CK(cudaLaunchKernel(h->kt.main[uni][h->launch.threads == 128 ? 0 : 1], dim3(h->launch.ctas),
-                        dim3(h->launch.threads), margs, 0, h->stream));
+    const unsigned char *bimg = (const unsigned char *)h->d_bimg;
+    int gN = h->grid_N;
+    void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
+    CK(cudaLaunchKernel(main_fn(h, h->launch.variant), dim3(h->launch.ctas), dim3(h->launch.threads), margs,
+                        is_grid(h) ? h->dyn_smem : 0, h->stream));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
     CK(cudaLaunchKernel(h->kt.refine[uni], dim3(refine_grid(h)), dim3(128), rargs, 0, h->stream));
     return TKDV_OK;
@@ -325,7 +371,8 @@ int check_status(tkdv_sampler *h) {
 void free_all(tkdv_sampler *h) {
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    for (void *p : {h->d_pts, h->d_stats, h->d_ring, h->d_ring_count, h->d_refine, h->d_counters, h->d_status})
+    for (void *p : {h->d_pts, h->d_stats, h->d_ring, h->d_ring_count, h->d_refine, h->d_counters, h->d_status,
+                    h->d_bimg})
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -357,13 +404,21 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (n_points < 1 || n_points > kMaxPoints)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "n_points must be in 1..64");
     if (opt->K < 1 || opt->K > kKMax) return fail(nullptr, TKDV_ERR_INVALID_ARG, "K must be in 1..64");
-    if (opt->h3_mode != TKDV_H3_TRIAD_F32)
-        return fail(nullptr, TKDV_ERR_UNSUPPORTED, "only the FP32 triad form is built into this library");
+    if (opt->h3_mode != TKDV_H3_TRIAD_F32 && opt->h3_mode != TKDV_H3_GRID_BF16X3)
+        return fail(nullptr, TKDV_ERR_INVALID_ARG, "unknown h3_mode");
+    int gridN = 0;
+    if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
+        gridN = opt->grid_N ? opt->grid_N : ((3 * opt->K + 1 + 31) / 32) * 32;
+        if (gridN % 32 != 0 || gridN <= 3 * opt->K || gridN > 256)
+            return fail(nullptr, TKDV_ERR_INVALID_ARG,
+                        "grid_N must be a multiple of 32, larger than 3K and at most 256");
+    }
     if (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "threads_per_cta must be 0, 128 or 256");
     tkdv_sampler *h = new tkdv_sampler();
     h->K = opt->K;
     h->kmax = kmax_for(opt->K);
+    h->grid_N = gridN;
     h->n_points = n_points;
     h->opt = *opt;
     h->pts.assign(points, points + n_points);
@@ -402,6 +457,39 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
         return bail(TKDV_ERR_CUDA);
     }
     h->launch.threads = opt->threads_per_cta ? opt->threads_per_cta : 256;
+    h->launch.variant = h->launch.threads == 128 ? 0 : 1;
+    if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
+        int major = 0;
+        e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+        if (e != cudaSuccess || major != 10) {
+            h->err = "the tensor-core grid form needs an sm_10x (tcgen05) device";
+            return bail(TKDV_ERR_UNSUPPORTED);
+        }
+        if (h->K <= 16)
+            grid_kernels_k16(&h->kg);
+        else if (h->K <= 32)
+            grid_kernels_k32(&h->kg);
+        else
+            grid_kernels_k64(&h->kg);
+        h->launch.threads = 128;
+        const size_t btile = (size_t)gridN * h->kg.ka * 2, atile = (size_t)128 * h->kg.ka * 2;
+        h->dyn_smem = 2 * btile + (size_t)h->kg.nwg * 2 * atile + 1024;
+        for (int u = 0; u < 2; ++u) {
+            e = cudaFuncSetAttribute(h->kg.main[u], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem);
+            if (e != cudaSuccess) {
+                h->err = std::string("grid kernel shared memory: ") + cudaGetErrorString(e);
+                return bail(TKDV_ERR_CUDA);
+            }
+        }
+        std::vector<unsigned char> img(2 * btile);
+        build_grid_image(h->K, h->kg.kmax, h->kg.ka, gridN, img.data());
+        e = cudaMalloc(&h->d_bimg, img.size());
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_bimg, img.data(), img.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            h->err = std::string("grid basis: ") + cudaGetErrorString(e);
+            return bail(e == cudaErrorMemoryAllocation ? TKDV_ERR_OOM : TKDV_ERR_CUDA);
+        }
+    }
     h->rec_bytes = record_bytes(h->K);
     const unsigned long long cap = opt->sample_capacity;
     auto alloc = [&](void **p, size_t bytes) -> int {
@@ -483,6 +571,14 @@ int sampler_sync(tkdv_sampler *h) {
     if (!h) return TKDV_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(h->stream));
     return check_status(h);
+}
+
+int sampler_set_trace(tkdv_sampler *h, void *dev_buf, uint64_t n) {
+    if (!h || (n && !dev_buf)) return TKDV_ERR_INVALID_ARG;
+    if (!is_grid(h)) return fail(h, TKDV_ERR_UNSUPPORTED, "the trace is written by the grid form only");
+    h->trace = n ? (float *)dev_buf : nullptr;
+    h->trace_n = n;
+    return TKDV_OK;
 }
 
 int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns) {
@@ -615,11 +711,17 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
     CK(cudaEventCreate(&e1));
     Launch best = h->launch;
     float best_ms = 1e30f;
-    for (int thr : {128, 256}) {
+    std::vector<int> var_list = {0, 1, 2};
+    if (is_grid(h)) var_list = {0};
+    (void)uni;
+    for (int var : var_list) {
+        const int thr = is_grid(h) ? 128 : kTriadVariantThreads[var];
         int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, h->kt.main[uni][thr == 128 ? 0 : 1], thr, 0));
+        int rc0 = max_ctas_per_sm(h, var, thr, &nb);
+        if (rc0) return rc0;
         for (int per = 1; per <= nb; ++per) {
             h->launch.threads = thr;
+            h->launch.variant = var;
             h->launch.ctas = per * h->num_sms;
             float ms_best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {

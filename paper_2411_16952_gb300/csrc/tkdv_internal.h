@@ -88,11 +88,15 @@ struct RunArgs {
     uint32_t chunk;                          // proposals per chunk
     int n_points;
     unsigned long long deadline_ns;          // 0: none; else per-CTA budget in ns
+    float *trace;                            // grid form: (log f/(Mg), T) of point 0's first trace_n
+    unsigned long long trace_n;              // proposals, or null
 };
 
 // Kernel table of one KMAX instantiation of the triad sampler.
 struct TriadKernels {
-    const void *main[2][2];  // [uniform][threads: 0 -> 128, 1 -> 256]
+    // [uniform][variant]: 0: 128 threads; 1: 256 threads; 2: 256 threads held
+    // to 128 registers (two CTAs per SM)
+    const void *main[2][3];
     const void *refine[2];
     const void *replay[2];
 };
@@ -101,6 +105,22 @@ void triad_kernels_k8(TriadKernels *t);
 void triad_kernels_k16(TriadKernels *t);
 void triad_kernels_k32(TriadKernels *t);
 void triad_kernels_k64(TriadKernels *t);
+
+// Kernel table of one KMAX instantiation of the grid (tensor-core) sampler.
+struct GridKernels {
+    const void *main[2];  // [uniform]
+    int nwg;              // tile buffers (TMEM accumulators) per 128-thread CTA
+    int kmax;             // modes per tile row half
+    int ka;               // contraction length (multiple of 64)
+};
+void grid_kernels_k16(GridKernels *t);
+void grid_kernels_k32(GridKernels *t);
+void grid_kernels_k64(GridKernels *t);
+// BF16 hi/lo image of the grid basis, already in the 128B-swizzled K-major
+// layout of shared memory: bytes [0, N*KA*2) hi, [N*KA*2, 2*N*KA*2) lo.
+void build_grid_image(int K, int kmax, int ka, int N, unsigned char *out);
+
+constexpr int kTriadVariantThreads[3] = {128, 256, 256};
 
 inline size_t record_bytes(int K) {
     size_t b = 32 + 8 * (size_t)K;

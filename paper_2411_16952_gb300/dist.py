@@ -1,0 +1,57 @@
+"""Multi-GPU sharding of the sampler (one process per GPU).
+
+Proposals are independent (Sec. IV.B: steps 2-5 need no communication), so
+ranks split the work with no exchange on the data path: either each rank
+takes a disjoint index range of every point (`shard_range`), or each rank
+samples its own point streams (`rank_point_id`).  The one collective is the
+final merge of statistics, a sum of integer counters and histograms plus a
+max (`merge_stats`), done once after the runs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+INT_KEYS = ("n_proposals", "n_accepted", "n_near_threshold", "n_refined", "n_envelope_violations",
+            "n_dropped", "n_fallback")
+
+
+def shard_range(total: int, rank: int, world: int):
+    """[start, start + count) of a range of `total` proposals for this rank
+    (contiguous, sizes differ by at most one)."""
+    base, extra = divmod(total, world)
+    start = rank * base + min(rank, extra)
+    return start, base + (1 if rank < extra else 0)
+
+
+def rank_point_id(rank: int, point: int, n_points: int) -> int:
+    """Philox point id of `point` on `rank`: disjoint streams across ranks."""
+    return rank * n_points + point
+
+
+def merge_stats(stats, group=None):
+    """Sum per-point statistics over ranks (torch.distributed all-reduce).
+    stats: list of dicts as returned by Sampler.stats(); returns merged dicts
+    with integer counters, histogram, exceedance counts and power sums added
+    and max_delta maximised."""
+    import torch
+    import torch.distributed as dist
+    P = len(stats)
+    ints = np.array([[s[k] for k in INT_KEYS] + list(s["hist"]) + list(s["exceed"]) for s in stats],
+                    dtype=np.int64)
+    sums = np.array([list(s["sum_u0"]) for s in stats], dtype=np.float64)
+    mx = np.array([s["max_delta"] for s in stats], dtype=np.float64)
+    ti, ts, tm = torch.from_numpy(ints), torch.from_numpy(sums), torch.from_numpy(mx)
+    dist.all_reduce(ti, group=group)
+    dist.all_reduce(ts, group=group)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX, group=group)
+    ints, sums, mx = ti.numpy(), ts.numpy(), tm.numpy()
+    nh = len(stats[0]["hist"])
+    out = []
+    for p in range(P):
+        d = {k: int(ints[p, i]) for i, k in enumerate(INT_KEYS)}
+        d["hist"] = ints[p, len(INT_KEYS):len(INT_KEYS) + nh].astype(np.uint64)
+        d["exceed"] = ints[p, len(INT_KEYS) + nh:].astype(np.uint64)
+        d["sum_u0"] = sums[p]
+        d["max_delta"] = float(mx[p])
+        out.append(d)
+    return out

@@ -1,0 +1,144 @@
+"""The learned proposal: MLP kernels against the FP64 oracle (oracle/mlp.py),
+and the learned-proposal sampler against the oracle's diagonal-Gaussian
+proposal."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_16952_gb300 import _build
+    _build.build()
+    import paper_2411_16952_gb300 as T
+    return T
+
+
+def theta_to_flat(th):
+    return np.concatenate([th["W1"].ravel(), th["b1"], th["W2"].ravel(), th["b2"], th["W3"].ravel(), th["b3"]])
+
+
+def flat_to_theta(v):
+    o, th = 0, {}
+    for name, shape in (("W1", (64, 4)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 64)),
+                        ("b3", (64,))):
+        n = int(np.prod(shape))
+        th[name] = np.asarray(v[o:o + n], dtype=np.float64).reshape(shape)
+        o += n
+    return th
+
+
+def projected_gaussian_s(rng, n, K, sigma2):
+    z = rng.standard_normal((n, 2 * K)) * np.sqrt(np.concatenate([sigma2, sigma2]))
+    x = z / np.linalg.norm(z, axis=1, keepdims=True)
+    return x[:, :K] ** 2 + x[:, K:] ** 2
+
+
+def setup_case(seed=0):
+    rng = np.random.default_rng(seed)
+    th = OM.init_theta(seed)
+    th["W3"] = rng.normal(0, 0.05, (64, 64))
+    th["b3"] = rng.normal(0, 0.05, 64)
+    th["b1"] = rng.normal(0, 0.1, 64)
+    pts = [(16, 20.0, 1.0, 60.0), (16, 40.0, 0.7, 30.0), (32, 30.0, 1.3, 200.0)]
+    Ks = [p[0] for p in pts]
+    feats = np.array([OM.features(K, bp, E0, r) for K, bp, E0, r in pts])
+    wp = [np.exp(rng.normal(0, 0.3, K)) for K in Ks]
+    s_list = [projected_gaussian_s(rng, 3000, K, np.exp(rng.normal(0, 0.3, K))) for K in Ks]
+    z_list = [rng.normal(0, 1.0, 3000) for _ in Ks]
+    return th, pts, Ks, feats, wp, s_list, z_list
+
+
+def test_features_match_oracle(T):
+    for K, bp, E0, r in [(16, 20.0, 1.0, 60.0), (32, 7.5, 1.9, 500.0), (64, 300.0, 0.5, 0.0)]:
+        assert np.allclose(T.tkdv_mlp_features(K, bp, E0, r), OM.features(K, bp, E0, r), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("tau", [0.0, 1.0, 0.3])
+def test_mlp_loss_and_gradient_match_oracle(T, tau):
+    """Forward, tempered NLL and backward kernels against FP64 backpropagation
+    with the same BF16-rounded parameters (oracle gradients are themselves
+    pinned by central differences)."""
+    th, pts, Ks, feats, wp, s_list, z_list = setup_case(1)
+    m = T.tkdv_mlp_create(3)
+    master = theta_to_flat(th).astype(np.float32)
+    T.tkdv_mlp_set_params(m, master)
+    _, bf = T.tkdv_mlp_get_params(m)
+    th_bf = flat_to_theta(OM.bf16_round(master))
+    assert np.array_equal(bf.astype(np.float64), OM.bf16_round(master))  # same rounding of the weights
+    T.tkdv_mlp_set_data(m, Ks, feats, wp, s_list, z_list)
+    loss, g = T.tkdv_mlp_step(m, lr=0.0, tau=tau, update=False, want_grad=True)
+    T.tkdv_mlp_destroy(m)
+    # the oracle sees the same FP32-rounded inputs
+    s32 = [s.astype(np.float32).astype(np.float64) for s in s_list]
+    z32 = [z.astype(np.float32).astype(np.float64) for z in z_list]
+    f32 = feats.astype(np.float32).astype(np.float64)
+    wp32 = [w.astype(np.float32).astype(np.float64) for w in wp]
+    J, grads = OM.loss_and_grad(th_bf, f32, Ks, wp32, s32, z32, None if tau <= 0 else tau)
+    assert abs(loss - J) <= 1e-4 * (1 + abs(J))
+    go = theta_to_flat(grads)
+    for name, (a, b) in {"W1": (0, 256), "b1": (256, 320), "W2": (320, 4416), "b2": (4416, 4480),
+                         "W3": (4480, 8576), "b3": (8576, 8640)}.items():
+        ga, gb = g[a:b].astype(np.float64), go[a:b]
+        assert np.max(np.abs(ga - gb)) <= 2e-3 * (np.max(np.abs(gb)) + 1e-6), name
+
+
+def test_mlp_inference_matches_oracle(T):
+    th, pts, Ks, feats, wp, s_list, z_list = setup_case(2)
+    m = T.tkdv_mlp_create(0)
+    master = theta_to_flat(th).astype(np.float32)
+    T.tkdv_mlp_set_params(m, master)
+    c = T.tkdv_mlp_infer(m, feats, Ks)
+    T.tkdv_mlp_destroy(m)
+    out, _ = OM.forward(flat_to_theta(OM.bf16_round(master)), feats.astype(np.float32).astype(np.float64))
+    for p, K in enumerate(Ks):
+        assert np.allclose(c[p, :K], OM.gauge(out[p], K), atol=1e-5)
+        assert abs(c[p, :K].sum()) < 1e-5 and np.all(c[p, K:] == 0)
+
+
+def test_fresh_network_is_the_paper_proposal(T):
+    m = T.tkdv_mlp_create(11)
+    c = T.tkdv_mlp_infer(m, np.array([T.tkdv_mlp_features(32, 40.0, 1.0, 225.0)]), [32])
+    T.tkdv_mlp_destroy(m)
+    assert np.all(c == 0)
+
+
+@pytest.mark.parametrize("K", [8, 16])
+def test_learned_proposal_sampler_matches_oracle(T, K):
+    """A diagonal Gaussian proposal with corrections c (here a fixed smooth
+    profile, the form the network outputs) gives the oracle's accept set."""
+    bp, E0, r = 20.0, 1.0, 60.0
+    k = np.arange(1, K + 1)
+    c = 0.4 * np.cos(math.pi * k / K)
+    c -= c.mean()
+    a = O.alpha_star(K, bp)
+    s2 = (1.0 / (1.0 + a * bp * k * k / K**3)) * np.exp(c)
+    pt = O.make_point(K, E0, bp, r, O.DIAG, sigma2=s2)
+    lm = O.log_M(pt, 2)
+    pt.logM = lm
+    S = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_LEARNED, point_id=4, logM=lm, log_var_correction=c)],
+                  sample_capacity=1 << 18)
+    _, _, s2_lib = S.point_info(0)
+    assert np.allclose(s2_lib, s2, rtol=1e-13)
+    n = 1 << 20
+    S.run_ranges([0], [n], 21)
+    st = S.stats()[0]
+    rec = S.samples(1 << 18)
+    S.close()
+    total, orec = O.run_accepted(pt, 21, 4, 0, n, cap=1 << 18)
+    g, o = set(rec["idx"].tolist()), set(orec["idx"].tolist())
+    diff = sorted(g ^ o)
+    if diff:
+        assert O.replay(pt, 21, 4, np.array(diff, dtype=np.uint64))["near"].all()
+    assert st["n_envelope_violations"] == 0 and abs(st["n_accepted"] - total) <= len(diff)
+    # the library's own envelope for the learned proposal agrees with the oracle's
+    assert abs(T.tkdv_log_M(K, bp, E0, r, s2) - lm) < 1e-8 * (1 + abs(lm))
