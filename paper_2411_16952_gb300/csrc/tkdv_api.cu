@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -734,6 +735,9 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
                 CK(cudaEventElapsedTime(&ms, e0, e1));
                 if (rep > 0) ms_best = std::min(ms_best, ms);
             }
+            if (std::getenv("TKDV_AUTOTUNE_LOG"))
+                std::fprintf(stderr, "tkdv autotune: variant %d threads %d ctas/SM %d -> %.3f ms\n", var, thr, per,
+                             (double)ms_best);
             if (ms_best < best_ms) {
                 best_ms = ms_best;
                 best = h->launch;
