@@ -231,6 +231,9 @@ def main():
     ap.add_argument("--ref-proposals", type=int, default=1 << 22)
     ap.add_argument("--ref-exact-envelope", action="store_true")
     ap.add_argument("--forms", default="", help="comma list of forms to time (default: all)")
+    ap.add_argument("--learn-accept", type=int, default=1 << 14, help="accepted samples per point to train on")
+    ap.add_argument("--learn-steps", type=int, default=200)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.impl == "reference":
@@ -255,14 +258,34 @@ def main():
     import datetime as dt
     clk = Clocks(local)  # started before any warm-up so that its start-up stays out of the timed steps
     forms = {"triad_f32_paper": (T.H3_TRIAD_F32, T.PROPOSAL_PAPER),
-             "grid_bf16x3_paper": (T.H3_GRID_BF16X3, T.PROPOSAL_PAPER)}
+             "grid_bf16x3_paper": (T.H3_GRID_BF16X3, T.PROPOSAL_PAPER),
+             "grid_bf16x3_learned": (T.H3_GRID_BF16X3, T.PROPOSAL_LEARNED)}
     if args.forms:
         forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
-    headline = "grid_bf16x3_paper" if "grid_bf16x3_paper" in forms else next(iter(forms))
+    headline = next((f for f in ("grid_bf16x3_learned", "grid_bf16x3_paper") if f in forms), next(iter(forms)))
+    learned_info = None
+    if "grid_bf16x3_learned" in forms:
+        # the learned proposal is trained (outside the timed region) on accepted
+        # samples of the same points, generated by the paper-proposal sampler
+        from paper_2411_16952_gb300 import learned as L
+        pts3 = [(bp, E0, r) for bp, r, _ in pts]
+        t_tr = time.perf_counter()
+        mlp, corr, hist, rows = L.train(K, pts3, n_accept=args.learn_accept, steps=args.learn_steps,
+                                        lr=2e-2, tau=0.0, seed=1, sampler_seed=rank + 1000, stream=stream)
+        L.close(mlp)
+        gains = [L.predicted_gain(K, p3, corr[i])[0] for i, p3 in enumerate(pts3)]
+        learned_info = {"train_seconds": time.perf_counter() - t_tr, "accepted_rows_per_point": rows.tolist(),
+                        "loss_first_last": [float(hist[0]), float(hist[-1])], "steps": args.learn_steps,
+                        "predicted_acceptance_gain": gains,
+                        "max_abs_correction": float(np.max(np.abs(corr)))}
     results = {}
     windows = []
     for fname, (mode, prop) in forms.items():
-        points = [T.make_point(bp, E0, r, prop, point_id=pid) for bp, r, pid in pts]
+        if prop == T.PROPOSAL_LEARNED:
+            points = [T.make_point(bp, E0, r, prop, point_id=pid, log_var_correction=corr[i])
+                      for i, (bp, r, pid) in enumerate(pts)]
+        else:
+            points = [T.make_point(bp, E0, r, prop, point_id=pid) for bp, r, pid in pts]
         S = T.Sampler(K, points, h3_mode=mode, grid_N=gN if mode == T.H3_GRID_BF16X3 else 0,
                       sample_capacity=1 << 21, stream=stream)
         if not args.no_autotune:
@@ -324,6 +347,42 @@ def main():
         results[fname] = res
     clocks = clk.stop(windows[0][0], windows[-1][1])
 
+    # the 64-point batch (uneven budgets 2^18..2^26, one persistent launch)
+    batch = None
+    if not args.no_batch:
+        from paper_2411_16952_gb300 import workloads
+        bw = workloads.batch_k32()
+        bpts = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]), T.PROPOSAL_PAPER,
+                             point_id=rank * 64 + p) for p in range(64)]
+        best_form = max((f for f in results if f != "grid_bf16x3_learned"),
+                        key=lambda f: results[f]["proposals_per_s"])
+        bmode = T.H3_GRID_BF16X3 if best_form.startswith("grid") else T.H3_TRIAD_F32
+        SB = T.Sampler(bw["K"], bpts, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,
+                       sample_capacity=1 << 22, stream=stream)
+        if not args.no_autotune:
+            SB.autotune(1 << 20)
+        for _ in range(args.warmup):
+            SB.run_budgets(bw["budgets"], 7)
+        SB.sync()
+        SB.reset()
+        bev = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            SB.run_budgets(bw["budgets"], 7)
+            e1.record(stream)
+            bev.append((e0, e1))
+        torch.cuda.synchronize()
+        bms = sum(a.elapsed_time(b_) for a, b_ in bev) / args.steps
+        bst = SB.stats()
+        bprop = sum(s["n_proposals"] for s in bst)
+        bacc = sum(s["n_accepted"] for s in bst)
+        batch = {"workload": bw["name"], "form": best_form, "proposals_per_step": bprop // args.steps,
+                 "ms_per_step": bms, "proposals_per_s": bprop / (bms * args.steps / 1e3),
+                 "accepted_per_s": bacc / (bms * args.steps / 1e3), "launch": SB.launch_config()}
+        SB.close()
+
     h = results[headline]
     form_kind = "grid" if headline.startswith("grid") else "triad"
     ops = alg_ops_per_proposal(K, form_kind, gN)
@@ -348,13 +407,16 @@ def main():
         "dtype": "bf16x3+f32" if form_kind == "grid" else "f32", "data": "synthetic",
         "proposals_per_s": h["proposals_per_s"], "acceptance": h["acceptance"],
         "headline_form": headline, "forms": results,
+        "vs_plain_fp32": h["accepted_per_s"] / results["triad_f32_paper"]["accepted_per_s"]
+        if "triad_f32_paper" in results else None,
+        "learned": learned_info, "batch_64pts": batch,
         "config": {"workload": wl["name"], "K": K, "grid_N": gN, "points": len(pts),
                    "proposals_per_point_per_step": n, "proposal": "paper",
                    "l2": "256 MiB buffer written between timed steps, outside the step events",
                    "parallelism": "points x index ranges, weak per GPU"},
         "roofline": roof,
         "e2e": h.get("e2e"),
-        "gpu_launches": 2 * args.steps * len(forms),
+        "gpu_launches": 2 * args.steps * len(forms) + (2 * args.steps if batch else 0),
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -160,8 +160,10 @@ template <int KMAX, bool UNIF>
 __device__ __noinline__ void redraw_record(unsigned char *rec, unsigned long long idx, uint32_t point, float H2,
                                            float H3, float u0, float delta, const float *sig, const float *act,
                                            uint32_t pid, int K, uint32_t k0, uint32_t k1) {
+    uint32_t rk[20];
+    round_keys(k0, k1, rk);
     Draw<KMAX> dr;
-    draw_fast<KMAX, UNIF>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), pid, k0, k1);
+    draw_fast<KMAX, UNIF>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), pid, rk);
     write_record<KMAX>(rec, idx, point, 0u, H2, H3, u0, delta, dr.x, dr.y, rsqrtf(dr.nrm2), K);
 }
 
@@ -180,8 +182,8 @@ struct GridPending {
 
 template <int KMAX, bool UNIF, int NBUF>
 __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
-    k_sample_grid(DevBufs B, RunArgs A, uint32_t k0, uint32_t k1, const unsigned char *__restrict__ bimg,
-                  int gridN) {
+    k_sample_grid(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1,
+                  const unsigned char *__restrict__ bimg, int gridN) {
     constexpr int NT = 128;
     constexpr int KA = GridShape<KMAX>::KA;
     constexpr int ATILE = GridShape<KMAX>::A_TILE;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
             const float tH = sc.cH * T;
             const float tQ = UNIF ? 0.f : sc.cQ * logf(g.zz * inv2);
             const float delta = ((tS + tH) + tQ) - sc.logM;
-            const float lnU = logf(u01f(accept_word(lo, hi, sc.pid, sc.K, k0, k1)));
+            const float lnU = logf(u01f(accept_word_rk(lo, hi, sc.pid, sc.K, A.rk)));
             const float d = lnU - delta;
             const float guard =
                 sc.ga + sc.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(lnU) + fabsf(sc.logM)) + sc.gh;
@@ -375,83 +377,89 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
         prev.valid = false;
         bool have_prev = false;
         int b = 0;
-        for (uint32_t i0 = 0; i0 < n_here; i0 += NT) {
+        // one extra trip with NBUF = 2 finishes the last tile (a single call
+        // site of consume keeps the code, and its instruction-cache footprint, small)
+        const uint32_t n_trips = (n_here + NT - 1) / NT + (NBUF == 2 ? 1u : 0u);
+        for (uint32_t trip = 0; trip < n_trips; ++trip) {
+            const bool produce = trip * NT < n_here;
+            const uint32_t i0 = trip * NT;
             const uint32_t i = i0 + (uint32_t)tid;
             GridPending cur;
-            cur.valid = i < n_here;
+            cur.valid = produce && i < n_here;
             cur.idx = cbase + i;
-            const uint32_t lo = (uint32_t)cur.idx, hi = (uint32_t)(cur.idx >> 32);
-            // Row of X in the contraction order: 16-byte chunk c holds
-            // (x, y) of modes 4c+1..4c+4, interleaved; chunk c is made from
-            // Philox blocks 2c and 2c+1 and stored at once (hi and lo).
-            unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)b * 2u * ATILE;
-            unsigned char *ga_lo = ga_hi + ATILE;
-            float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, u0raw = 0.f;
-#pragma unroll
-            for (int cch = 0; cch < KMAX / 4; ++cch) {
-                float v[8];
-#pragma unroll
-                for (int jj = 0; jj < 2; ++jj) {
-                    const int j = 2 * cch + jj;
-                    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, sc.pid), k0, k1);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int m = 2 * j + h;
-                        float rho, zc, zs;
-                        box_muller_f32(h ? w.z : w.x, h ? w.w : w.y, rho, zc, zs);
-                        const float s = UNIF ? s_act[m] : s_sig[m];
-                        const float xm = s * zc, ym = s * zs;
-                        v[4 * jj + 2 * h] = xm;
-                        v[4 * jj + 2 * h + 1] = ym;
-                        const float sk = (s * s) * rho;
-                        nrm2 += sk;
-                        Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
-                        zz = fmaf(s_act[m], rho, zz);
-                        u0raw += xm;
+            if (produce) {
+                const uint32_t lo = (uint32_t)cur.idx, hi = (uint32_t)(cur.idx >> 32);
+                // Row of X in the contraction order: 16-byte chunk c holds
+                // (x, y) of modes 4c+1..4c+4, interleaved; chunk c is made from
+                // Philox blocks 2c and 2c+1 and stored at once (hi and lo).
+                unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)b * 2u * ATILE;
+                unsigned char *ga_lo = ga_hi + ATILE;
+                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, u0raw = 0.f;
+    #pragma unroll
+                for (int cch = 0; cch < KMAX / 4; ++cch) {
+                    float v[8];
+    #pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = 2 * cch + jj;
+                        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk);
+    #pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int m = 2 * j + h;
+                            float rho, zc, zs;
+                            box_muller_f32(h ? w.z : w.x, h ? w.w : w.y, rho, zc, zs);
+                            const float s = UNIF ? s_act[m] : s_sig[m];
+                            const float xm = s * zc, ym = s * zs;
+                            v[4 * jj + 2 * h] = xm;
+                            v[4 * jj + 2 * h + 1] = ym;
+                            const float sk = (s * s) * rho;
+                            nrm2 += sk;
+                            Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
+                            zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
+                            u0raw += xm;
+                        }
                     }
+                    uint4 hv, lv;
+                    split8(v, hv, lv);
+                    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)cch * 8u, 128u);
+                    *reinterpret_cast<uint4 *>(ga_hi + off) = hv;
+                    *reinterpret_cast<uint4 *>(ga_lo + off) = lv;
                 }
-                uint4 hv, lv;
-                split8(v, hv, lv);
-                const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)cch * 8u, 128u);
-                *reinterpret_cast<uint4 *>(ga_hi + off) = hv;
-                *reinterpret_cast<uint4 *>(ga_lo + off) = lv;
-            }
-            cur.nrm2 = nrm2;
-            cur.Sraw = Sraw;
-            cur.zz = zz;
-            cur.u0raw = u0raw;
-            fence_async_smem();
-            __syncthreads();
-            if (!s_abort) {
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint32_t ah = a0 + (uint32_t)b * 2u * ATILE, al = ah + ATILE;
-                    const uint32_t dt = tmem0 + (uint32_t)b * tcols;
-#pragma unroll
-                    for (int ks = 0; ks < KA / 16; ++ks) {
-                        const uint32_t koff = (uint32_t)((ks & 3) * 32);  // 16 BF16 = 32 bytes per step
-                        const uint32_t aat = (uint32_t)(ks >> 2) * 128u * 128u;
-                        const uint32_t bat = (uint32_t)(ks >> 2) * (uint32_t)gridN * 128u;
-                        const uint64_t dah = sw128_desc(ah + aat + koff), dal = sw128_desc(al + aat + koff);
-                        const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
-                        umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                        umma_bf16(dt, dah, dbl, idesc, 1u);
-                        umma_bf16(dt, dal, dbh, idesc, 1u);
+                cur.nrm2 = nrm2;
+                cur.Sraw = Sraw;
+                cur.zz = zz;
+                cur.u0raw = u0raw;
+                fence_async_smem();
+                __syncthreads();
+                if (!s_abort) {
+                    if (tid == 0) {
+                        tc_fence_after();
+                        const uint32_t ah = a0 + (uint32_t)b * 2u * ATILE, al = ah + ATILE;
+                        const uint32_t dt = tmem0 + (uint32_t)b * tcols;
+    #pragma unroll
+                        for (int ks = 0; ks < KA / 16; ++ks) {
+                            const uint32_t koff = (uint32_t)((ks & 3) * 32);  // 16 BF16 = 32 bytes per step
+                            const uint32_t aat = (uint32_t)(ks >> 2) * 128u * 128u;
+                            const uint32_t bat = (uint32_t)(ks >> 2) * (uint32_t)gridN * 128u;
+                            const uint64_t dah = sw128_desc(ah + aat + koff), dal = sw128_desc(al + aat + koff);
+                            const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
+                            umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                            umma_bf16(dt, dah, dbl, idesc, 1u);
+                            umma_bf16(dt, dal, dbh, idesc, 1u);
+                        }
+                        umma_commit(smem_u32(&s_mbar[b]));
                     }
-                    umma_commit(smem_u32(&s_mbar[b]));
+                    waits_pending[b] = true;
                 }
-                waits_pending[b] = true;
             }
             if (NBUF == 2) {
                 if (have_prev) consume(prev, b ^ 1);
                 prev = cur;
-                have_prev = true;
+                have_prev = produce;
                 b ^= 1;
             } else {
                 consume(cur, b);
             }
         }
-        if (NBUF == 2 && have_prev) consume(prev, b ^ 1);
 
         uint32_t key = fkey(maxd);
         key = __reduce_max_sync(0xffffffffu, key);

@@ -215,7 +215,29 @@ int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
     int nb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads,
                                                      is_grid(h) ? h->dyn_smem : 0));
-    if (is_grid(h)) nb = std::min(nb, 512 / grid_tmem_cols(h));  // TMEM: 512 columns per SM
+    if (is_grid(h)) {
+        // The grid kernel's residency follows from its own limits: shared
+        // memory (with the per-block reservation), allocated registers, and
+        // the 512 TMEM columns of an SM.  (The occupancy query above has been
+        // seen to answer one CTA where two are resident.)
+        cudaFuncAttributes fa{};
+        int smem_sm = 0, resv = 0, regs_sm = 0;
+        CK(cudaFuncGetAttributes(&fa, main_fn(h, variant)));
+        CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+        CK(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, h->device));
+        CK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->device));
+        const size_t smem_blk = h->dyn_smem + fa.sharedSizeBytes + (size_t)resv;
+        const int regs_thr = (fa.numRegs + 7) / 8 * 8;
+        const int regs_blk = ((regs_thr * 32 + 255) / 256 * 256) * ((threads + 31) / 32);
+        int by_smem = (int)((size_t)smem_sm / smem_blk);
+        int by_regs = regs_blk > 0 ? regs_sm / regs_blk : 1;
+        int by_tmem = 512 / grid_tmem_cols(h);
+        const int own = std::max(1, std::min(by_smem, std::min(by_regs, by_tmem)));
+        if (std::getenv("TKDV_AUTOTUNE_LOG"))
+            std::fprintf(stderr, "tkdv occupancy: query %d, shared memory %d, registers %d (%d/thread), TMEM %d\n",
+                         nb, by_smem, by_regs, fa.numRegs, by_tmem);
+        nb = own;
+    }
     *out = nb;
     return TKDV_OK;
 }
@@ -261,6 +283,10 @@ int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned l
     a.trace_n = h->trace ? h->trace_n : 0ull;
     h->key0 = (uint32_t)seed;
     h->key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {  // Philox4x32-10 key schedule (Weyl increments)
+        a.rk[2 * r] = h->key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = h->key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     return TKDV_OK;
 }
 
@@ -477,6 +503,9 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
         h->dyn_smem = 2 * btile + (size_t)h->kg.nwg * 2 * atile + 1024;
         for (int u = 0; u < 2; ++u) {
             e = cudaFuncSetAttribute(h->kg.main[u], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem);
+            if (e == cudaSuccess)  // the largest shared-memory carve-out, so that two CTAs fit on an SM
+                e = cudaFuncSetAttribute(h->kg.main[u], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) {
                 h->err = std::string("grid kernel shared memory: ") + cudaGetErrorString(e);
                 return bail(TKDV_ERR_CUDA);

@@ -142,3 +142,44 @@ def test_learned_proposal_sampler_matches_oracle(T, K):
     assert st["n_envelope_violations"] == 0 and abs(st["n_accepted"] - total) <= len(diff)
     # the library's own envelope for the learned proposal agrees with the oracle's
     assert abs(T.tkdv_log_M(K, bp, E0, r, s2) - lm) < 1e-8 * (1 + abs(lm))
+
+
+def test_trained_network_gain(T):
+    """What the trained network gains over the paper's Sigma.
+
+    Trains on accepted samples of four K = 16 points (Table 1 regime), then for
+    each point: the predicted acceptance gain exp(log M_paper - log M_learned)
+    (exact, because the corrections have mean zero), the measured acceptance
+    ratio over 2^24 proposals per proposal kind, and the ensemble statistics of
+    the two proposals (the paper's Sigma judges the learned one).  In this
+    family of proposals the gain is small (the paper's Sigma is near the best
+    per-mode variance profile); the test pins prediction = measurement and
+    that the learned proposal samples the same Gibbs measure."""
+    from paper_2411_16952_gb300 import learned as L
+    K = 16
+    points = [(40.0, 1.0, 60.0), (20.0, 1.0, 120.0), (60.0, 1.0, 40.0), (20.0, 1.0, 60.0)]
+    m, c, hist, rows = L.train(K, points, n_accept=1 << 14, steps=300, lr=2e-2, tau=0.0, seed=1)
+    L.close(m)
+    assert hist[-1] <= hist[0] + 1e-9 and np.all(rows >= 1 << 13)
+    n = 1 << 24
+    for p, pt in enumerate(points):
+        gain, lm_p, lm_l = L.predicted_gain(K, pt, c[p])
+        bp, E0, r = pt
+        Sp = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=100 + p)], sample_capacity=4)
+        Sl = T.Sampler(K, L.learned_points(K, [pt], c[p:p + 1], point_id0=200 + p), sample_capacity=4)
+        Sp.run(n, 5)
+        Sl.run(n, 5)
+        sp, sl = Sp.stats()[0], Sl.stats()[0]
+        Sp.close()
+        Sl.close()
+        assert sl["n_envelope_violations"] == 0 and sp["n_envelope_violations"] == 0
+        ap, al = sp["n_accepted"] / n, sl["n_accepted"] / n
+        se = math.sqrt(ap * (1 - ap) / n) / ap + math.sqrt(al * (1 - al) / n) / al
+        assert abs(al / ap - gain) <= 4 * se * gain, (pt, al / ap, gain)
+        assert gain > 0.9
+        # same Gibbs measure: mean, variance and skewness of u0 within 3 SE
+        nn = min(sp["n_accepted"], sl["n_accepted"])
+        assert abs(sp["skew"] - sl["skew"]) <= 3 * math.sqrt(12.0 / nn)
+        assert abs(sp["var"] - sl["var"]) <= 3 * sp["var"] * math.sqrt(2 * max(sp["kurt"] - 1, 1) / nn)
+        print("point %s: predicted gain %.3f, measured %.3f +- %.3f, c in [%.3f, %.3f]" % (
+            pt, gain, al / ap, se * gain, c[p].min(), c[p].max()))
