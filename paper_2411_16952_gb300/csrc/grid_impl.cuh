@@ -160,10 +160,8 @@ template <int KMAX, bool UNIF>
 __device__ __noinline__ void redraw_record(unsigned char *rec, unsigned long long idx, uint32_t point, float H2,
                                            float H3, float u0, float delta, const float *sig, const float *act,
                                            uint32_t pid, int K, uint32_t k0, uint32_t k1) {
-    uint32_t rk[20];
-    round_keys(k0, k1, rk);
     Draw<KMAX> dr;
-    draw_fast<KMAX, UNIF>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), pid, rk);
+    draw_fast<KMAX, UNIF>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), pid, k0, k1);
     write_record<KMAX>(rec, idx, point, 0u, H2, H3, u0, delta, dr.x, dr.y, rsqrtf(dr.nrm2), K);
 }
 
@@ -310,7 +308,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
             const float tH = sc.cH * T;
             const float tQ = UNIF ? 0.f : sc.cQ * logf(g.zz * inv2);
             const float delta = ((tS + tH) + tQ) - sc.logM;
-            const float lnU = logf(u01f(accept_word_rk(lo, hi, sc.pid, sc.K, A.rk)));
+            const float lnU = logf(u01f(accept_word(lo, hi, sc.pid, sc.K, k0, k1)));
             const float d = lnU - delta;
             const float guard =
                 sc.ga + sc.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(lnU) + fabsf(sc.logM)) + sc.gh;
@@ -355,13 +353,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
                 if (acc) {
                     const float u0 = sc.u0s * g.u0raw * inv;
-                    atomicAdd(&s_hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
-                    atomicAdd(&s_exc[exc_bin(u0, sc.ea)], 1u);
-                    const float u2 = u0 * u0;
-                    atomicAdd(&s_q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
-                    atomicAdd(&s_q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
-                    atomicAdd(&s_q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
-                    atomicAdd(&s_q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+                    tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
                     const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
                     if (slot < B.ring_cap) {
                         redraw_record<KMAX, UNIF>(B.ring + slot * B.rec_bytes, g.idx, (uint32_t)p, sc.E0 * S,
@@ -395,13 +387,13 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                 unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)b * 2u * ATILE;
                 unsigned char *ga_lo = ga_hi + ATILE;
                 float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, u0raw = 0.f;
-    #pragma unroll
+    #pragma unroll 2
                 for (int cch = 0; cch < KMAX / 4; ++cch) {
                     float v[8];
     #pragma unroll
                     for (int jj = 0; jj < 2; ++jj) {
                         const int j = 2 * cch + jj;
-                        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk);
+                        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, sc.pid), k0, k1);
     #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int m = 2 * j + h;

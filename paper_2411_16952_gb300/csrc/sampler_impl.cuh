@@ -43,28 +43,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// The same with the ten round keys given (rk[2r], rk[2r+1] for round r); the
-// sampler kernels pass them from their parameter block, so the key schedule
-// costs no instruction per block.
-__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *__restrict__ rk) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
-    }
-    return c;
-}
-
-__host__ __device__ __forceinline__ void round_keys(uint32_t k0, uint32_t k1, uint32_t *rk) {
-    for (int r = 0; r < 10; ++r) {
-        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-    }
-}
-
 // (2 floor(w/512) + 1) 2^-24: (w >> 8) | 1 == 2 floor(w/512) + 1, exact in FP32.
 __device__ __forceinline__ float u01f(uint32_t w) {
     return __uint2float_rn((w >> 8) | 1u) * 0x1p-24f;
@@ -144,14 +122,14 @@ struct Draw {
 template <int KMAX, bool UNIF>
 __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
                                           uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
-                                          const uint32_t *__restrict__ rk) {
+                                          uint32_t k0, uint32_t k1) {
     d.nrm2 = 0.f;
     d.Sraw = 0.f;
     d.zz = 0.f;
     d.u0raw = 0.f;
 #pragma unroll
     for (int j = 0; j < (KMAX + 1) / 2; ++j) {
-        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, idx_lo, idx_hi, pid), rk);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, idx_lo, idx_hi, pid), k0, k1);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
@@ -228,10 +206,6 @@ __device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, u
 __device__ __forceinline__ uint32_t accept_word(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                                 int K, uint32_t k0, uint32_t k1) {
     return philox4x32_10(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), k0, k1).x;
-}
-__device__ __forceinline__ uint32_t accept_word_rk(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, int K,
-                                                   const uint32_t *__restrict__ rk) {
-    return philox4x32_10_rk(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), rk).x;
 }
 
 __device__ __forceinline__ int hist_bin(float u0, float a, float b) {
@@ -337,6 +311,20 @@ __device__ __forceinline__ void write_record(unsigned char *rec, unsigned long l
     }
 }
 
+// Statistics of one accepted draw into the CTA's shared-memory partials.  Out
+// of line: accepted draws are rare, and keeping this code out of the hot loop
+// keeps that loop's instruction-cache footprint small.
+static __device__ __noinline__ void tally_accepted(float u0, float ha, float hb, float ea, uint32_t *s_hist,
+                                            uint32_t *s_exc, unsigned long long *s_q) {
+    atomicAdd(&s_hist[hist_bin(u0, ha, hb)], 1u);
+    atomicAdd(&s_exc[exc_bin(u0, ea)], 1u);
+    const float u2 = u0 * u0;
+    atomicAdd(&s_q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
+    atomicAdd(&s_q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
+    atomicAdd(&s_q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+    atomicAdd(&s_q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+}
+
 // ---- the persistent sampler ----------------------------------------------
 template <int KMAX, bool UNIF, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
@@ -393,8 +381,8 @@ __global__ void __launch_bounds__(NT, MINB)
             const unsigned long long idx = base + i;
             const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
             Draw<KMAX> dr;
-            draw_fast<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, A.rk);
-            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk);
+            draw_fast<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, k0, k1);
+            const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
             bool defer = valid && fabsf(f.d) < f.guard;
             if (valid) maxd = fmaxf(maxd, f.delta);
@@ -435,13 +423,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
                 if (acc) {
                     const float u0 = sc.u0s * dr.u0raw * f.inv;
-                    atomicAdd(&s_hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
-                    atomicAdd(&s_exc[exc_bin(u0, sc.ea)], 1u);
-                    const float u2 = u0 * u0;
-                    atomicAdd(&s_q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
-                    atomicAdd(&s_q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
-                    atomicAdd(&s_q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
-                    atomicAdd(&s_q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+                    tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
                     const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
                     if (slot < B.ring_cap) {
                         write_record<KMAX>(B.ring + slot * B.rec_bytes, idx, (uint32_t)p, 0u, sc.E0 * f.S,
@@ -542,11 +524,9 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
     const int K = sc.K;
     const unsigned long long id = idx[i];
     const uint32_t lo = (uint32_t)id, hi = (uint32_t)(id >> 32);
-    uint32_t rk[20];
-    round_keys(k0, k1, rk);
     Draw<KMAX> dr;
-    draw_fast<KMAX, UNIF>(dr, P->sigma, P->act, lo, hi, sc.pid, rk);
-    const uint32_t wa = accept_word_rk(lo, hi, sc.pid, K, rk);
+    draw_fast<KMAX, UNIF>(dr, P->sigma, P->act, lo, hi, sc.pid, k0, k1);
+    const uint32_t wa = accept_word(lo, hi, sc.pid, K, k0, k1);
     const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
     double *row = out + i * (unsigned long long)(8 + 2 * K);
     if (fabsf(f.d) < f.guard) {

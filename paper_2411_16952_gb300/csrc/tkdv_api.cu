@@ -283,10 +283,6 @@ int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned l
     a.trace_n = h->trace ? h->trace_n : 0ull;
     h->key0 = (uint32_t)seed;
     h->key1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {  // Philox4x32-10 key schedule (Weyl increments)
-        a.rk[2 * r] = h->key0 + (uint32_t)r * 0x9E3779B9u;
-        a.rk[2 * r + 1] = h->key1 + (uint32_t)r * 0xBB67AE85u;
-    }
     return TKDV_OK;
 }
 

@@ -85,7 +85,6 @@ struct RunArgs {
     unsigned long long idx0[kMaxPoints];
     unsigned long long count[kMaxPoints];
     uint32_t chunk_prefix[kMaxPoints + 1];  // cumulative chunk counts
-    uint32_t rk[20];                         // Philox round keys of the run's seed
     uint32_t chunk;                          // proposals per chunk
     int n_points;
     unsigned long long deadline_ns;          // 0: none; else per-CTA budget in ns

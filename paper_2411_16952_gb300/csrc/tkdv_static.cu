@@ -187,10 +187,6 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
     A.chunk_prefix[0] = 0;
     A.chunk_prefix[1] = (uint32_t)((n_proposals + chunk - 1) / chunk);
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {  // Philox4x32-10 key schedule, read by the sampler kernel
-        A.rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-        A.rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-    }
 
     // The array keeps the previous call's contents: clear the header (the
     // statistics, counters and status must start at zero), then upload the
