@@ -61,6 +61,17 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
     return common + triad
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per proposal of
+# the sampler kernels, from one ncu capture each of the small case
+# (--n-per-point 4194304, 8 points: 3.36e7 proposals per launch); the kernels
+# read no per-proposal input, so traffic scales with the proposals processed.
+# Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_PER_PROPOSAL = {
+    "grid": (286720.0 / (8 * 4194304), "ncu --set full capture prof_grid10 (k_sample_grid<32,0,2>)"),
+    "triad": (83200.0 / (8 * 4194304), "ncu --set full capture prof_triad10 (k_sample_triad<32,0,256,1>)"),
+}
+
+
 def tensor_flops_per_proposal(K: int, grid_N: int) -> int:
     """Three BF16 products of a 2K-padded-to-64 row with the 2K x N basis."""
     ka = (2 * K + 63) // 64 * 64
@@ -390,8 +401,12 @@ def main():
     props_per_step = h["proposals_per_s"] * step_s
     achieved = ops * props_per_step / step_s / 1e12
     peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    tr = TRAFFIC_PER_PROPOSAL.get(form_kind)
+    traffic = None if tr is None or tr[0] is None else tr[0] * props_per_step
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-            "traffic": None, "ops_per_proposal": ops, "kernel": "k_sample_%s" % form_kind,
+            "traffic": traffic, "traffic_source": tr[1] if tr else None,
+            "algorithmic_bytes_per_launch": h["acceptance"] * props_per_step * T.tkdv_record_bytes(K) + 2304 * len(pts),
+            "ops_per_proposal": ops, "kernel": "k_sample_%s" % form_kind,
             "note": "ideal thread-instruction count per proposal (bench.py alg_ops_per_proposal); peak = "
                     "152 SM x 128 lanes x max SM clock (%s sm_max_mhz)" % peak_src}
     if form_kind == "grid":
