@@ -76,7 +76,9 @@ def lib():
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.orc_uniform.argtypes = [C.c_uint32]
             L.orc_uniform.restype = C.c_double
-            L.orc_box_muller.argtypes = [C.c_uint32, C.c_uint32, dp, dp]
+            L.orc_uniform_ext.argtypes = [C.c_uint32, C.c_uint32, u32p, C.c_uint64, C.c_uint32]
+            L.orc_uniform_ext.restype = C.c_double
+            L.orc_box_muller.argtypes = [C.c_double, C.c_double, dp, dp]
             L.orc_stream.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, dp, dp]
             for f in ("orc_H2", "orc_H3_double", "orc_H3_triple"):
                 getattr(L, f).argtypes = [C.c_int, C.c_double, dp]
@@ -131,9 +133,15 @@ def uniform(w):
     return lib().orc_uniform(int(w) & 0xFFFFFFFF)
 
 
-def box_muller(w1, w2):
+def uniform_ext(w, g, seed, idx, point_id):
+    """Uniform of word w at stream position g of proposal idx, lowest bucket refined."""
+    k = (C.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    return lib().orc_uniform_ext(int(w) & 0xFFFFFFFF, int(g), k, int(idx), int(point_id) & 0xFFFFFFFF)
+
+
+def box_muller(u1, u2):
     a, b = C.c_double(), C.c_double()
-    lib().orc_box_muller(int(w1) & 0xFFFFFFFF, int(w2) & 0xFFFFFFFF, C.byref(a), C.byref(b))
+    lib().orc_box_muller(float(u1), float(u2), C.byref(a), C.byref(b))
     return a.value, b.value
 
 

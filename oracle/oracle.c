@@ -82,12 +82,36 @@ double orc_uniform(uint32_t w)
     return (2.0 * (double)(w >> 9) + 1.0) * 0x1p-24;
 }
 
+/* The uniform of the word at position g (4 * block + word) of proposal idx,
+ * with its lowest bucket refined.  orc_uniform alone puts every u < 2^-23 at
+ * 2^-24; that caps the Box-Muller radius (-2 ln u <= 33.3) and the accept
+ * test (ln U >= -16.6), so a draw whose log ratio is below -16.6 could never
+ * be accepted although Sec. IV.B accepts it with probability e^Delta.  A word
+ * in the lowest bucket (w < 512) is therefore followed, level by level, by
+ * word 0 of the Philox block with counter (2^31 + L 2^24 + g, idx_lo, idx_hi,
+ * point_id), L = 1, 2: U = 2^-23 u(w_1) if w_1 >= 512, else 2^-46 u(w_2).
+ * U is then uniform on (0, 1) with 23 bits of relative resolution down to
+ * 2^-70. */
+double orc_uniform_ext(uint32_t w, uint32_t g, const uint32_t key[2], uint64_t idx, uint32_t point_id)
+{
+    if (w >= 512u)
+        return orc_uniform(w);
+    double scale = 1.0;
+    for (uint32_t level = 1; level <= 2; ++level) {
+        uint32_t ctr[4] = {0x80000000u + (level << 24) + g, (uint32_t)idx, (uint32_t)(idx >> 32), point_id};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        scale *= 0x1p-23;
+        if (out[0] >= 512u || level == 2)
+            return scale * orc_uniform(out[0]);
+    }
+    return 0.0; /* not reached */
+}
+
 /* Box-Muller: two independent standard normals from two uniforms; these are
  * the draws from the standard normal d(gamma) of Eq. (14). */
-void orc_box_muller(uint32_t w1, uint32_t w2, double *z_cos, double *z_sin)
+void orc_box_muller(double u1, double u2, double *z_cos, double *z_sin)
 {
-    double u1 = orc_uniform(w1);
-    double u2 = orc_uniform(w2);
     double rad = sqrt(-2.0 * log(u1));
     double ang = 2.0 * M_PI * u2;
     *z_cos = rad * cos(ang);
@@ -105,14 +129,15 @@ void orc_stream(int K, uint64_t seed, uint32_t point_id, uint64_t idx, double *z
         ctr[2] = (uint32_t)(idx >> 32);
         ctr[3] = point_id;
         orc_philox4x32_10(ctr, key, w);
-        orc_box_muller(w[2 * h], w[2 * h + 1], &z[k - 1], &z[K + k - 1]);
+        double u1 = orc_uniform_ext(w[2 * h], (uint32_t)(4 * j + 2 * h), key, idx, point_id);
+        orc_box_muller(u1, orc_uniform(w[2 * h + 1]), &z[k - 1], &z[K + k - 1]);
     }
     ctr[0] = (uint32_t)((K + 1) / 2);
     ctr[1] = (uint32_t)idx;
     ctr[2] = (uint32_t)(idx >> 32);
     ctr[3] = point_id;
     orc_philox4x32_10(ctr, key, w);
-    *u_acc = orc_uniform(w[0]);
+    *u_acc = orc_uniform_ext(w[0], (uint32_t)(4 * ((K + 1) / 2)), key, idx, point_id);
 }
 
 /* ---------------------------------------------------------------------------

@@ -68,8 +68,11 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* Uniform in (0,1) from one 32-bit word: (2*floor(w/512) + 1) / 2^24. */
 double orc_uniform(uint32_t w);
-/* Box-Muller pair from two words. */
-void orc_box_muller(uint32_t w1, uint32_t w2, double *z_cos, double *z_sin);
+/* The uniform of word w at stream position g of proposal idx, its lowest
+ * bucket (w < 512) refined from further Philox blocks down to 2^-70. */
+double orc_uniform_ext(uint32_t w, uint32_t g, const uint32_t key[2], uint64_t idx, uint32_t point_id);
+/* Box-Muller pair from two uniforms. */
+void orc_box_muller(double u1, double u2, double *z_cos, double *z_sin);
 /* The 2K standard normals and the accept uniform of proposal idx (stream layout). */
 void orc_stream(int K, uint64_t seed, uint32_t point_id, uint64_t idx, double *z, double *u_acc);
 

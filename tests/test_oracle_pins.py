@@ -75,6 +75,33 @@ def test_uniform_map_properties():
     assert O.uniform(0) == 2.0**-24 and O.uniform(2**32 - 1) == 1.0 - 2.0**-24
 
 
+def test_uniform_tail_is_refined():
+    """The lowest bucket (u < 2^-23) is not a point mass: the accept test
+    ln U < Delta must be able to accept draws with Delta < ln 2^-24 (they are
+    accepted with probability e^Delta), and the Box-Muller radius must not be
+    capped at -2 ln 2^-24."""
+    sp = pytest.importorskip("scipy.stats")
+    seed, pid, g = 12345, 7, 4 * 16
+    # words above the lowest bucket keep the one-word map
+    for w in (512, 1000, 2**31, 2**32 - 1):
+        assert O.uniform_ext(w, g, seed, 3, pid) == O.uniform(w)
+    n = 20000
+    t = np.array([O.uniform_ext(0, g, seed, i, pid) for i in range(n)])
+    assert np.all(t > 2.0**-70) and np.all(t < 2.0**-23)
+    # every word of the bucket gives the same refinement (it depends on the counter only)
+    assert O.uniform_ext(511, g, seed, 5, pid) == t[5]
+    # within the bucket, 2^23 U is uniform on (0, 1): P(ln U < c | bucket) = 2^23 e^c
+    v = t * 2.0**23
+    assert sp.kstest(v, "uniform").pvalue > 1e-3
+    for c in (-17.0, -20.0):
+        p = math.exp(c) * 2.0**23
+        k = int(np.sum(np.log(t) < c))
+        assert abs(k - n * p) < 5 * math.sqrt(n * p), (c, k, n * p)
+    # the refinement of another stream position is another draw
+    t2 = np.array([O.uniform_ext(0, g + 2, seed, i, pid) for i in range(2000)])
+    assert abs(np.corrcoef(t2, t[:2000])[0, 1]) < 4 / math.sqrt(2000)
+
+
 def test_stream_normals_are_standard_normal():
     sp = pytest.importorskip("scipy.stats")
     K = 16
