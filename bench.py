@@ -272,6 +272,9 @@ def main():
              "grid_bf16x3_paper": (T.H3_GRID_BF16X3, T.PROPOSAL_PAPER),
              "grid_bf16x3_learned": (T.H3_GRID_BF16X3, T.PROPOSAL_LEARNED)}
     if args.forms:
+        unknown = set(args.forms.split(",")) - set(forms)
+        if unknown:
+            raise SystemExit("unknown form(s) %s; known: %s" % (sorted(unknown), sorted(forms)))
         forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
     headline = next((f for f in ("grid_bf16x3_learned", "grid_bf16x3_paper") if f in forms), next(iter(forms)))
     learned_info = None

@@ -24,7 +24,12 @@
  *     Mode k takes the Box-Muller pair in words 2h, 2h+1 of block
  *     j = (k-1)/2, h = (k-1) % 2 (cosine -> X_k, sine -> X_{K+k}).  The accept
  *     uniform is word 0 of block ceil(K/2).  A word w maps to
- *     (2 floor(w/512) + 1) 2^-24.  Accept iff ln U < log f/(M g).
+ *     (2 floor(w/512) + 1) 2^-24, except that a radius or accept word in the
+ *     lowest bucket (w < 512) is refined by word 0 of the blocks with counter
+ *     (2^31 + L 2^24 + g, idx_lo, idx_hi, point_id), g = 4 j + word, L = 1, 2:
+ *     U = 2^-23 u(w_1) if w_1 >= 512, else 2^-46 u(w_2); so U stays uniform
+ *     down to 2^-70 and a draw with log f/(M g) < ln 2^-24 can be accepted.
+ *     Accept iff ln U < log f/(M g).
  *     Given (parameters, seed, point_id, log M) the accepted set of an index
  *     range is therefore a fixed set, whatever the launch shape.
  *   - Return values: 0 on success, a negative TKDV_ERR_* code otherwise;
@@ -54,7 +59,17 @@ extern "C" {
 #define TKDV_ERR_TIMEOUT (-5)     /* a device wait hit its iteration limit; results of that run are void */
 #define TKDV_ERR_UNSUPPORTED (-6) /* requested form not available on this device */
 #define TKDV_ERR_ENVELOPE (-7)    /* envelope search failed (non-finite log M) */
-#define TKDV_ERR_TOO_LARGE (-8)   /* sampler_run_static: more proposals than its fixed scratch holds */
+#define TKDV_ERR_TOO_LARGE (-8)   /* tkdv_check_radius_error: diagnostic (the paper has no counterpart).  The
+   FP32 fast path computes the Box-Muller radius rho = -2 ln u of the uniform
+   map's 2^23 values with the hardware base-2 logarithm; its accept guard band
+   assumes |rho_f32 - rho| <= 2^-21 + 2^-21 rho.  This runs all 2^23 values on
+   the current device against an FP64 logarithm and returns the largest ratio
+   of the error to that bound (at most 1 if the assumption holds) and a word
+   that attains it (worst_word may be NULL).  Allocates 8 bytes of device
+   memory for the call.  Errors: INVALID_ARG (max_ratio NULL), OOM, CUDA. */
+int tkdv_check_radius_error(double *max_ratio, uint32_t *worst_word);
+
+/* sampler_run_static: more proposals than its fixed scratch holds */
 
 /* ---- proposal kinds (Sec. III) ------------------------------------------ */
 #define TKDV_PROPOSAL_UNIFORM 0 /* uniform measure mu0 on the sphere (Eq. 15); the naive baseline */
@@ -68,6 +83,7 @@ extern "C" {
 #define TKDV_MAX_POINTS 64
 #define TKDV_HIST_BINS 256
 #define TKDV_N_EXCEED 25
+#define TKDV_KMAX 64
 
 /* One parameter point (Sec. IV.A: K, E0, beta', C3/C2 are the only parameters). */
 typedef struct {
@@ -116,6 +132,9 @@ typedef struct {
     uint64_t hist[TKDV_HIST_BINS];  /* u0 histogram on [hist_lo, hist_hi] */
     double hist_lo, hist_hi;        /* -/+ sqrt(2 K E0 / pi), the largest |u| on the sphere */
     uint64_t exceed[TKDV_N_EXCEED]; /* accepted with u0 > 0.25 i sqrt(E0/pi), i = 0..24 (Sec. V.D) */
+    double spectrum[TKDV_KMAX];     /* sum over accepted of s_k = xhat_k^2 + xhat_{K+k}^2 = |u_k|^2 2pi/E0,
+                                       k = 1..K (0 beyond K); spectrum / n_accepted is the mean power
+                                       spectrum of Sec. V.A.  Each term is rounded to 2^-28. */
 } tkdv_stats;
 
 /* Accepted-sample record, as stored in the device ring and returned by
@@ -176,6 +195,17 @@ int sampler_stats(tkdv_sampler *h, tkdv_stats *out, int n_out);
 int sampler_samples(tkdv_sampler *h, void *dst, int dst_on_device, uint64_t max_records,
                     uint64_t *n_out);
 
+/* sampler_field_maxima: the largest surface displacement of each of the
+   first min(max_records, kept) records (in the order sampler_samples returns
+   them) on the 2K-point grid xi_j = -pi + pi j / K of Sec. V.D:
+   umax[i] = max_j u(xi_j), u from Eqs. (8), (16); jmax[i] = the maximising j
+   (the smallest on ties; jmax may be NULL).  The field with the largest umax
+   among m accepted fields is the "1-in-m event" of Figs. 8-11.  umax and jmax
+   are host arrays of max_records entries; *n_out receives the count.  Runs
+   one kernel on the handle's stream (synchronises); allocates 8 bytes per
+   record of device memory for the call.  Errors: INVALID_ARG, OOM, CUDA. */
+int sampler_field_maxima(tkdv_sampler *h, uint64_t max_records, double *umax, int32_t *jmax, uint64_t *n_out);
+
 /* sampler_reset: zero statistics, the record ring and the running indices. */
 int sampler_reset(tkdv_sampler *h);
 
@@ -193,7 +223,9 @@ int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns);
 /* sampler_set_trace: grid form only (tcgen05 contraction).  Later runs write,
    for each of point 0's first n proposals of the run (index idx0[0] + i),
    the pair (log f/(Mg), T) as two floats at dev_buf[2i], where
-   H3 = 2 pi (E0/2pi)^{3/2} T (Eq. 42 in these units).  dev_buf is the
+   H3 = 2 pi (E0/2pi)^{3/2} T (Eq. 42 in these units).  A proposal with a
+   refined word (about 2K+1 in 2^23, see the stream rule above) is decided in
+   the FP64 pass only and traced as two NaNs.  dev_buf is the
    caller's device buffer of 2n floats; n = 0 switches the trace off.
    Errors: INVALID_ARG, UNSUPPORTED (triad form). */
 int sampler_set_trace(tkdv_sampler *h, void *dev_buf, uint64_t n);

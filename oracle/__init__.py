@@ -80,6 +80,9 @@ def lib():
             L.orc_uniform_ext.restype = C.c_double
             L.orc_box_muller.argtypes = [C.c_double, C.c_double, dp, dp]
             L.orc_stream.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, dp, dp]
+            L.orc_tail_scan.argtypes = [C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64, C.c_int,
+                                        C.POINTER(C.c_uint64), C.c_uint64]
+            L.orc_tail_scan.restype = C.c_uint64
             for f in ("orc_H2", "orc_H3_double", "orc_H3_triple"):
                 getattr(L, f).argtypes = [C.c_int, C.c_double, dp]
                 getattr(L, f).restype = C.c_double
@@ -137,6 +140,14 @@ def uniform_ext(w, g, seed, idx, point_id):
     """Uniform of word w at stream position g of proposal idx, lowest bucket refined."""
     k = (C.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     return lib().orc_uniform_ext(int(w) & 0xFFFFFFFF, int(g), k, int(idx), int(point_id) & 0xFFFFFFFF)
+
+
+def tail_scan(K, seed, point_id, idx0, n, which=3, cap=1 << 16):
+    """Indices of [idx0, idx0+n) with a radius (which & 1) or accept (which & 2)
+    word in the lowest bucket of the uniform map; returns (indices, total)."""
+    out = np.zeros(cap, dtype=np.uint64)
+    tot = lib().orc_tail_scan(K, seed, point_id, idx0, n, which, out.ctypes.data_as(C.POINTER(C.c_uint64)), cap)
+    return out[:min(tot, cap)], int(tot)
 
 
 def box_muller(u1, u2):

@@ -140,6 +140,39 @@ void orc_stream(int K, uint64_t seed, uint32_t point_id, uint64_t idx, double *z
     *u_acc = orc_uniform_ext(w[0], (uint32_t)(4 * ((K + 1) / 2)), key, idx, point_id);
 }
 
+uint64_t orc_tail_scan(int K, uint64_t seed, uint32_t point_id, uint64_t idx0, uint64_t n, int which,
+                       uint64_t *out, uint64_t cap)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint64_t found = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t idx = idx0 + i;
+        uint32_t ctr[4] = {0, (uint32_t)idx, (uint32_t)(idx >> 32), point_id}, w[4];
+        int hit = 0;
+        if (which & 1) {
+            for (int j = 0; j < (K + 1) / 2 && !hit; ++j) {
+                ctr[0] = (uint32_t)j;
+                orc_philox4x32_10(ctr, key, w);
+                /* the radius words of block j: word 0 (mode 2j+1) and word 2 (mode 2j+2) */
+                if (w[0] < 512u || (2 * j + 2 <= K && w[2] < 512u))
+                    hit = 1;
+            }
+        }
+        if ((which & 2) && !hit) {
+            ctr[0] = (uint32_t)((K + 1) / 2);
+            orc_philox4x32_10(ctr, key, w);
+            if (w[0] < 512u)
+                hit = 1;
+        }
+        if (hit) {
+            if (found < cap)
+                out[found] = idx;
+            ++found;
+        }
+    }
+    return found;
+}
+
 /* ---------------------------------------------------------------------------
  * Hamiltonian pieces on the sphere.  xh is the real spectral vector
  * [xh_1..xh_K | xh_{K+1}..xh_{2K}] of Sec. II.C, and the microstate is

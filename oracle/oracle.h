@@ -75,6 +75,11 @@ double orc_uniform_ext(uint32_t w, uint32_t g, const uint32_t key[2], uint64_t i
 void orc_box_muller(double u1, double u2, double *z_cos, double *z_sin);
 /* The 2K standard normals and the accept uniform of proposal idx (stream layout). */
 void orc_stream(int K, uint64_t seed, uint32_t point_id, uint64_t idx, double *z, double *u_acc);
+/* Indices in [idx0, idx0+n) whose stream has a word in the lowest bucket of
+ * the uniform map: which = 1 radius words, 2 the accept word, 3 either.
+ * Writes the first `cap` to out; returns how many there are. */
+uint64_t orc_tail_scan(int K, uint64_t seed, uint32_t point_id, uint64_t idx0, uint64_t n, int which,
+                       uint64_t *out, uint64_t cap);
 
 double orc_H2(int K, double E0, const double *xh);
 double orc_H3_double(int K, double E0, const double *xh);

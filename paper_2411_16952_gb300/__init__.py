@@ -30,6 +30,7 @@ H3_TRIAD_F32, H3_GRID_BF16X3 = 0, 1
 MAX_POINTS = 64
 HIST_BINS = 256
 N_EXCEED = 25
+KMAX = 64
 
 EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler_run",
             "sampler_run_budgets", "sampler_run_ranges", "sampler_stats", "sampler_samples",
@@ -68,7 +69,7 @@ class tkdv_stats(C.Structure):
                 ("alpha_star", C.c_double), ("sum_u0", C.c_double * 4), ("mean", C.c_double),
                 ("var", C.c_double), ("skew", C.c_double), ("kurt", C.c_double),
                 ("hist", C.c_uint64 * HIST_BINS), ("hist_lo", C.c_double), ("hist_hi", C.c_double),
-                ("exceed", C.c_uint64 * N_EXCEED)]
+                ("exceed", C.c_uint64 * N_EXCEED), ("spectrum", C.c_double * KMAX)]
 
 
 _lock = threading.Lock()
@@ -123,6 +124,8 @@ def lib():
             L.sampler_destroy.restype = None
             L.tkdv_alpha_star.argtypes = [i, d, dp]
             L.tkdv_log_M.argtypes = [i, d, d, d, dp, dp]
+            L.tkdv_check_radius_error.argtypes = [dp, C.POINTER(C.c_uint32)]
+            L.sampler_field_maxima.argtypes = [vp, u64, dp, C.POINTER(C.c_int32), u64p]
             L.sampler_run_static.argtypes = [i, C.POINTER(tkdv_point), u64, u64, u64, vp, u64, u64p,
                                              C.POINTER(tkdv_stats), vp]
             _lib = L
@@ -138,6 +141,25 @@ def _check(rc, handle=None):
 # ---- the C entry points under their own names ------------------------------
 def tkdv_record_bytes(K):
     return int(lib().tkdv_record_bytes(K))
+
+
+def sampler_field_maxima(h, max_records):
+    """(umax, j) of the first kept records on the 2K-point grid xi_j = -pi + pi j/K."""
+    umax = np.zeros(max(int(max_records), 1))
+    jm = np.zeros(max(int(max_records), 1), dtype=np.int32)
+    n = C.c_uint64()
+    _check(lib().sampler_field_maxima(h, max_records, _dptr(umax), jm.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      C.byref(n)), h)
+    return umax[:n.value], jm[:n.value]
+
+
+def tkdv_check_radius_error():
+    """(largest ratio of error to its bound 2^-21 + 2^-21 rho, a word attaining
+    it) of the fast path's FP32 radius -2 ln u over all 2^23 values of the
+    uniform map (runs on the device)."""
+    err, w = C.c_double(), C.c_uint32()
+    _check(lib().tkdv_check_radius_error(C.byref(err), C.byref(w)))
+    return err.value, w.value
 
 
 def tkdv_alpha_star(K, beta_p):
@@ -401,7 +423,8 @@ def _stats_dict(s):
             "alpha_star": s.alpha_star, "sum_u0": np.array(s.sum_u0[:]), "mean": s.mean,
             "var": s.var, "skew": s.skew, "kurt": s.kurt,
             "hist": np.array(s.hist[:], dtype=np.uint64), "hist_lo": s.hist_lo,
-            "hist_hi": s.hist_hi, "exceed": np.array(s.exceed[:], dtype=np.uint64)}
+            "hist_hi": s.hist_hi, "exceed": np.array(s.exceed[:], dtype=np.uint64),
+            "spectrum": np.array(s.spectrum[:])}
 
 
 def decode_records(buf, K):
@@ -479,6 +502,26 @@ class Sampler:
 
     def point_info(self, p=0):
         return sampler_point_info(self.h, p, self.K)
+
+    def field_maxima(self, max_records=1 << 20):
+        """Largest displacement (and its grid index j, xi_j = -pi + pi j/K) of
+        each kept record, in the order samples() returns them."""
+        return sampler_field_maxima(self.h, max_records)
+
+    def extreme_field(self, m=500, point=0, max_records=1 << 20):
+        """The 1-in-m event of Figs. 8-11: among the first m accepted fields
+        of `point` (by proposal index) the one with the largest displacement
+        on the 2K-point grid.  Returns a dict (idx, umax, xi, xhat) or None
+        when fewer than m fields were kept."""
+        rec = self.samples(max_records)
+        umax, jm = self.field_maxima(max_records)
+        sel = np.nonzero(rec["point"] == point)[0]
+        if len(sel) < m:
+            return None
+        sel = sel[np.argsort(rec["idx"][sel], kind="stable")[:m]]
+        b = sel[int(np.argmax(umax[sel]))]
+        return {"idx": int(rec["idx"][b]), "umax": float(umax[b]),
+                "xi": float(-np.pi + np.pi * jm[b] / self.K), "xhat": rec["xhat"][b].astype(np.float64)}
 
     def replay(self, p, idx, seed):
         return sampler_replay(self.h, p, self.K, idx, seed)

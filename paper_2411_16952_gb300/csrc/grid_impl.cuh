@@ -153,18 +153,6 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// The record of an accepted draw needs its projected state, which the grid
-// form does not keep in registers: regenerate it (accepted draws only; out
-// of line so that it adds no register pressure to the main loop).
-template <int KMAX, bool UNIF>
-__device__ __noinline__ void redraw_record(unsigned char *rec, unsigned long long idx, uint32_t point, float H2,
-                                           float H3, float u0, float delta, const float *sig, const float *act,
-                                           uint32_t pid, int K, uint32_t k0, uint32_t k1) {
-    Draw<KMAX> dr;
-    draw_fast<KMAX, UNIF>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), pid, k0, k1);
-    write_record<KMAX>(rec, idx, point, 0u, H2, H3, u0, delta, dr.x, dr.y, rsqrtf(dr.nrm2), K);
-}
-
 // ---- the persistent grid-form sampler --------------------------------------
 // One warpgroup (128 threads) per CTA.  With NBUF = 2 the BF16 tiles and the
 // TMEM accumulators are double-buffered: after the MMAs of tile t are issued
@@ -174,8 +162,9 @@ __device__ __noinline__ void redraw_record(unsigned char *rec, unsigned long lon
 // 1024-byte aligned.
 struct GridPending {
     unsigned long long idx;
-    float nrm2, Sraw, zz, u0raw;
+    float nrm2, Sraw, zz, esum;
     bool valid;
+    bool tail;  // a radius word in the lowest bucket of the uniform map
 };
 
 template <int KMAX, bool UNIF, int NBUF>
@@ -189,6 +178,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
     __shared__ uint32_t s_hist[kHistBins];
     __shared__ uint32_t s_exc[kExcBins];
     __shared__ unsigned long long s_q[4];
+    __shared__ unsigned long long s_spec[KMAX];
     __shared__ uint32_t s_cnt[4];
     __shared__ uint32_t s_maxd;
     __shared__ uint32_t s_chunk;
@@ -212,6 +202,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
         for (uint32_t i = tid; i < (uint32_t)NBUF * 2 * ATILE / 16; i += NT) az[i] = make_uint4(0, 0, 0, 0);
     }
     for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
+    for (int e = tid; e < KMAX; e += NT) s_spec[e] = 0ull;
     if (tid < kExcBins) s_exc[tid] = 0;
     if (tid < 4) {
         s_q[tid] = 0ull;
@@ -285,13 +276,23 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                     waits_pending[b] = false;
                     tc_fence_after();
                     const uint32_t taddr = tmem0 + (uint32_t)b * tcols + lane_off;
+                    // sum of U^3 in four packed accumulators (columns e mod 8),
+                    // so that no single chain of dependent FMAs is long
+                    f32x2_t cq[4] = {0ull, 0ull, 0ull, 0ull};
                     for (int cb = 0; cb < gridN; cb += 32) {
                         float u[32];
                         tmem_ld32(taddr + (uint32_t)cb, u);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) cube = fmaf(u[e] * u[e], u[e], cube);
+                        for (int e = 0; e < 32; e += 2) {
+                            const f32x2_t uu = pk2(u[e], u[e + 1]);
+                            cq[(e >> 1) & 3] = fma2(mul2(uu, uu), uu, cq[(e >> 1) & 3]);
+                        }
                     }
+                    float c[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) upk2(cq[q], c[2 * q], c[2 * q + 1]);
+                    cube = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
                     tc_fence_before();
                 } else {
                     atomicOr(B.status, kStatusMbarTimeout);
@@ -308,16 +309,21 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
             const float tH = sc.cH * T;
             const float tQ = UNIF ? 0.f : sc.cQ * logf(g.zz * inv2);
             const float delta = ((tS + tH) + tQ) - sc.logM;
-            const float lnU = logf(u01f(accept_word(lo, hi, sc.pid, sc.K, k0, k1)));
+            const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
+            const float lnU = -0.5f * rho_fast(wa);
             const float d = lnU - delta;
-            const float guard =
-                sc.ga + sc.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(lnU) + fabsf(sc.logM)) + sc.gh;
-            bool defer = usable && fabsf(d) < guard;
-            if (usable) maxd = fmaxf(maxd, delta);
+            const float guard = fmaf(
+                sc.ge * g.esum, inv,
+                fmaf(sc.gq, inv2, sc.ga + sc.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(lnU) + fabsf(sc.logM)) + sc.gh));
+            // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
+            const bool tail = g.tail || wa < kTailBucket;
+            bool defer = usable && (fabsf(d) < guard || tail);
+            if (usable && !tail) maxd = fmaxf(maxd, delta);
             const unsigned long long li = g.idx - A.idx0[p];
             if (A.trace && p == 0 && usable && li < A.trace_n) {
-                A.trace[2 * li] = delta;
-                A.trace[2 * li + 1] = T;
+                // a draw with a refined tail word is decided in FP64 only: NaN here
+                A.trace[2 * li] = tail ? __int_as_float(0x7fc00000) : delta;
+                A.trace[2 * li + 1] = tail ? __int_as_float(0x7fc00000) : T;
             }
             const unsigned md = __ballot_sync(0xffffffffu, defer);
             if (md) {
@@ -352,21 +358,22 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                 }
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
                 if (acc) {
-                    const float u0 = sc.u0s * g.u0raw * inv;
-                    tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
                     const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
-                    if (slot < B.ring_cap) {
-                        redraw_record<KMAX, UNIF>(B.ring + slot * B.rec_bytes, g.idx, (uint32_t)p, sc.E0 * S,
-                                                  sc.h3s * T, u0, delta, s_sig, s_act, sc.pid, sc.K, k0, k1);
-                    } else {
+                    unsigned char *rec = nullptr;
+                    if (slot < B.ring_cap)
+                        rec = B.ring + slot * B.rec_bytes;
+                    else
                         atomicAdd(&s_cnt[2], 1u);
-                    }
+                    // the grid form keeps no projected state: emit_accepted draws it again
+                    emit_accepted<KMAX, UNIF>(P, g.idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
+                                              s_spec, rec);
                 }
             }
         };
 
         GridPending prev;
         prev.valid = false;
+        prev.tail = false;
         bool have_prev = false;
         int b = 0;
         // one extra trip with NBUF = 2 finishes the last tile (a single call
@@ -378,6 +385,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
             const uint32_t i = i0 + (uint32_t)tid;
             GridPending cur;
             cur.valid = produce && i < n_here;
+            cur.tail = false;
             cur.idx = cbase + i;
             if (produce) {
                 const uint32_t lo = (uint32_t)cur.idx, hi = (uint32_t)(cur.idx >> 32);
@@ -386,7 +394,8 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                 // Philox blocks 2c and 2c+1 and stored at once (hi and lo).
                 unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)b * 2u * ATILE;
                 unsigned char *ga_lo = ga_hi + ATILE;
-                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, u0raw = 0.f;
+                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
+                uint32_t wmin = 0xFFFFFFFFu;
     #pragma unroll 2
                 for (int cch = 0; cch < KMAX / 4; ++cch) {
                     float v[8];
@@ -397,17 +406,17 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
     #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int m = 2 * j + h;
-                            float rho, zc, zs;
-                            box_muller_f32(h ? w.z : w.x, h ? w.w : w.y, rho, zc, zs);
                             const float s = UNIF ? s_act[m] : s_sig[m];
-                            const float xm = s * zc, ym = s * zs;
+                            float rho, xm, ym, rr;
+                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                            wmin = min(wmin, h ? w.z : w.x);
+                            esum = fmaf(s, rr, esum);
                             v[4 * jj + 2 * h] = xm;
                             v[4 * jj + 2 * h + 1] = ym;
                             const float sk = (s * s) * rho;
                             nrm2 += sk;
                             Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
                             zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
-                            u0raw += xm;
                         }
                     }
                     uint4 hv, lv;
@@ -419,7 +428,8 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
                 cur.nrm2 = nrm2;
                 cur.Sraw = Sraw;
                 cur.zz = zz;
-                cur.u0raw = u0raw;
+                cur.esum = esum;
+                cur.tail = wmin < kTailBucket;
                 fence_async_smem();
                 __syncthreads();
                 if (!s_abort) {
@@ -471,6 +481,12 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : 1)
         if (tid < 4 && s_q[tid]) {
             atomicAdd(&st->q[tid], s_q[tid]);
             s_q[tid] = 0ull;
+        }
+        for (int e = tid; e < KMAX; e += NT) {
+            if (s_spec[e]) {
+                atomicAdd(&st->spec[e], s_spec[e]);
+                s_spec[e] = 0ull;
+            }
         }
         if (tid == 0) {
             atomicAdd(&st->n_prop, (unsigned long long)n_here);

@@ -8,7 +8,8 @@
 //   3. scale by sigma_k (Eqs. 24-26); |x|^2, S|x|^2 and Q|x|^2 accumulate as
 //      the normals are made, so the projection xhat = x/|x| (Sec. IV.B) is
 //      applied as scalar factors, never to the 2K components;
-//   4. H3 by the double sum of Eq. (42) with the k <-> n-k symmetry folded;
+//   4. H3 by the double sum of Eq. (42) with the k <-> n-k symmetry folded,
+//      two products per packed FP32 instruction;
 //   5. log f/(M g) = -beta' S/K^2 + beta' r/(E0 K^2) H3 + K ln Q - log M
 //      (Eqs. 40 and 43);
 //   6. accept iff ln U < log f/(M g).  The FP32 result decides only when the
@@ -43,29 +44,90 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// (2 floor(w/512) + 1) 2^-24: (w >> 8) | 1 == 2 floor(w/512) + 1, exact in FP32.
+// (2 floor(w/512) + 1) 2^-24, exact in FP32: the float 1 + m 2^-23 with
+// m = w >> 9 is built from its bits, and subtracting 1 - 2^-24 (a float) is
+// exact (Sterbenz), leaving (2m + 1) 2^-24.
 __device__ __forceinline__ float u01f(uint32_t w) {
-    return __uint2float_rn((w >> 8) | 1u) * 0x1p-24f;
+    return __uint_as_float(0x3f800000u | (w >> 9)) - 0x1.fffffep-1f;
 }
 __device__ __forceinline__ double u01d(uint32_t w) {
     return (double)((w >> 8) | 1u) * 0x1p-24;
 }
 
-// Box-Muller pair in FP32: rho = -2 ln u1 (the squared radius), and
-// (z_cos, z_sin) = sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
+// The map above puts every u < 2^-23 at 2^-24.  That would cap the
+// Box-Muller radius (rho <= -2 ln 2^-24 = 33.3) and the accept test
+// (ln U >= -16.6, so a draw with Delta below that could never be accepted,
+// although the rule accepts it with probability e^Delta).  A word in the
+// lowest bucket (w < kTailBucket) is refined by word 0 of the Philox blocks
+// with counter (kTailCtr + L 2^24 + g, idx_lo, idx_hi, point_id), L = 1, 2,
+// where g = 4 * block + word is the position of the refined word in the
+// proposal's stream: U = 2^-23 u(w_1) if w_1 is above the lowest bucket, else
+// 2^-46 u(w_2).  U is then uniform with 23 bits of relative resolution down to
+// 2^-70.  The FP32 fast path only detects such words (1 in 2^23) and sends the
+// proposal to the FP64 pass, which applies the refinement.
+constexpr uint32_t kTailBucket = 512u;
+constexpr uint32_t kTailCtr = 0x80000000u;
+
+static __device__ __noinline__ double u01d_tail(uint32_t g, uint32_t lo, uint32_t hi, uint32_t pid, uint32_t k0,
+                                                uint32_t k1) {
+    const uint32_t w1 = philox4x32_10(make_uint4(kTailCtr + (1u << 24) + g, lo, hi, pid), k0, k1).x;
+    if (w1 >= kTailBucket) return 0x1p-23 * u01d(w1);
+    const uint32_t w2 = philox4x32_10(make_uint4(kTailCtr + (2u << 24) + g, lo, hi, pid), k0, k1).x;
+    return 0x1p-46 * u01d(w2);
+}
+
+// The uniform of word w at stream position g, its lowest bucket refined.
+__device__ __forceinline__ double u01d_ext(uint32_t w, uint32_t g, uint32_t lo, uint32_t hi, uint32_t pid,
+                                           uint32_t k0, uint32_t k1) {
+    return w >= kTailBucket ? u01d(w) : u01d_tail(g, lo, hi, pid, k0, k1);
+}
+
+// 2 pi (u - 1/2) for u = u01f(w), rounded once: (1 + m 2^-23) - 3/2 is exact,
+// and 2 pi (u - 1/2) = 2 pi ((1 + m 2^-23) - 3/2) + 2 pi 2^-24 takes one FMA.
+__device__ __forceinline__ float angle_f(uint32_t w) {
+    constexpr float k2Pi = 6.28318530717958647692f;
+    return fmaf(k2Pi, __uint_as_float(0x3f800000u | (w >> 9)) - 1.5f, k2Pi * 0x1p-24f);
+}
+
+// Squared Box-Muller radius rho = -2 ln u for u = u01f(w), FP32.
+// rho_fast (the decision path) takes the hardware base-2 logarithm, whose
+// documented error is at most 2 ulp below 1/2 and 2^-22 absolute on [1/2, 2):
+// |rho_fast - rho| <= kRhoAbsErr + kRhoRelErr rho (tkdv_check_radius_error
+// measures it over all 2^23 values); the decision guard takes the absolute
+// part per draw from sum_m sigma_m / sqrt(rho_m).  The floor keeps rho
+// positive where that error could cross zero.
+__device__ __forceinline__ float rho_fast(uint32_t w) {
+    return fmaxf(__log2f(u01f(w)) * -1.38629436111989061883f, 0x1p-25f);
+}
+// rho_acc (the outputs of accepted draws) is rho_fast below u = 1 - 2^-9
+// (there rho >= 2^-8 and the absolute error is a small relative one) and
+// above it the series -2 ln(1 - t) = 2t (1 + t/2 + t^2/3), t = 1 - u = u01f(~w)
+// exact (the map is symmetric), truncated below 2e-9 relative.
+__device__ __forceinline__ float rho_acc(uint32_t w) {
+    const float t = u01f(~w);
+    const float ser = (2.f * t) * fmaf(t, fmaf(t, 1.f / 3.f, 0.5f), 1.f);
+    return w >= 0xFF800000u ? ser : rho_fast(w);
+}
+// 1/sqrt(rho) above which a draw holds a radius of the series range (rho < 2^-8)
+constexpr float kSmallRhoRsqrt = 15.5f;
+
+// Box-Muller pair in FP32, scaled by s: rho = -2 ln u1 (the squared radius),
+// and (x, y) = s sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
 // exactly to 2 pi (u2 - 1/2) in (-pi, pi), where the hardware sine/cosine have
 // an absolute error below 2^-21.4, and cos(t - pi) = -cos t, sin(t - pi) =
-// -sin t restore the signs; sqrt(rho) = rho * rsqrt(rho).  The FP32 decision
-// guard covers these errors (draws near the threshold are redone in FP64).
-__device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float &rho, float &zc, float &zs) {
-    const float u1 = u01f(w1);
-    const float u2 = u01f(w2);
-    rho = -2.f * logf(u1);
-    const float nrad = -(rho * rsqrtf(rho));
+// -sin t restore the signs; s sqrt(rho) = (s rho) rsqrt(rho).  The FP32
+// decision guard covers these errors (draws near the threshold are redone in
+// FP64).  rr returns 1/sqrt(rho).
+template <bool ACC>
+__device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float s, float &rho, float &x, float &y,
+                                               float &rr) {
+    rho = ACC ? rho_acc(w1) : rho_fast(w1);
+    rr = rsqrtf(rho);
+    const float a = (-s * rho) * rr;
     float sn, cs;
-    __sincosf(6.28318530717958647692f * (u2 - 0.5f), &sn, &cs);
-    zc = nrad * cs;
-    zs = nrad * sn;
+    __sincosf(angle_f(w2), &sn, &cs);
+    x = a * cs;
+    y = a * sn;
 }
 
 // Order-preserving map float -> uint32 (for atomicMax on signed floats).
@@ -82,7 +144,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // Scalar constants of the current point, held in registers.
 struct Scal {
-    float cS, cH, cQ, logM, u0s, h3s, E0, ga, gr, gh, ha, hb, ea;
+    float cS, cH, cQ, logM, u0s, h3s, E0, ga, gr, gh, ge, gq, ha, hb, ea;
     uint32_t pid;
     int K;
 };
@@ -99,6 +161,8 @@ __device__ __forceinline__ Scal load_scal(const PointConst *P) {
     s.ga = __ldg(&P->guard_abs);
     s.gr = __ldg(&P->guard_rel);
     s.gh = __ldg(&P->guard_h);
+    s.ge = __ldg(&P->guard_e);
+    s.gq = __ldg(&P->guard_q);
     s.ha = __ldg(&P->hist_a);
     s.hb = __ldg(&P->hist_b);
     s.ea = __ldg(&P->exc_a);
@@ -112,14 +176,17 @@ __device__ __forceinline__ Scal load_scal(const PointConst *P) {
 template <int KMAX>
 struct Draw {
     float x[KMAX], y[KMAX];
-    float nrm2;   // |x|^2
-    float Sraw;   // sum k^2 (x_k^2 + y_k^2)  = S |x|^2
-    float zz;     // sum over active modes of the normals' squares = Q |x|^2
-    float u0raw;  // sum_k x_k                = u(0) |x| / u0s
+    float nrm2;     // |x|^2
+    float Sraw;     // sum k^2 (x_k^2 + y_k^2)  = S |x|^2
+    float zz;       // sum over active modes of the normals' squares = Q |x|^2
+    float u0raw;    // sum_k x_k                = u(0) |x| / u0s
+    uint32_t wmin;  // smallest radius word: below kTailBucket the draw needs the FP64 pass
+    float esum;     // sum_m sigma_m / sqrt(rho_m): scales the radius-error guard
+    float rrmax;    // largest 1/sqrt(rho_m): above kSmallRhoRsqrt outputs need rho_acc
 };
 
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
-template <int KMAX, bool UNIF>
+template <int KMAX, bool UNIF, bool ACC = false>
 __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
                                           uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                           uint32_t k0, uint32_t k1) {
@@ -127,6 +194,9 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
     d.Sraw = 0.f;
     d.zz = 0.f;
     d.u0raw = 0.f;
+    d.wmin = 0xFFFFFFFFu;
+    d.esum = 0.f;
+    d.rrmax = 0.f;
 #pragma unroll
     for (int j = 0; j < (KMAX + 1) / 2; ++j) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)j, idx_lo, idx_hi, pid), k0, k1);
@@ -134,10 +204,12 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
             if (m < KMAX) {
-                float rho, zc, zs;
-                box_muller_f32(h ? w.z : w.x, h ? w.w : w.y, rho, zc, zs);
                 const float s = UNIF ? act[m] : sig[m];
-                const float xm = s * zc, ym = s * zs;
+                float rho, xm, ym, rr;
+                box_muller_f32<ACC>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                d.wmin = min(d.wmin, h ? w.z : w.x);
+                d.esum = fmaf(s, rr, d.esum);
+                d.rrmax = fmaxf(d.rrmax, s > 0.f ? rr : 0.f);
                 d.x[m] = xm;
                 d.y[m] = ym;
                 const float sk = (s * s) * rho;
@@ -150,33 +222,69 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
     }
 }
 
+// ---- packed FP32 pairs (sm_100+ f32x2 instructions: one issue, two lanes) ----
+typedef unsigned long long f32x2_t;
+__device__ __forceinline__ f32x2_t pk2(float lo, float hi) {
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2_t fma2(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Step 4: T = sum_{n=2}^{KMAX} x_n A_n + y_n B_n, with
 //   A_n = sum_{k=1}^{n-1} x_k x_{n-k} - y_k y_{n-k},
 //   B_n = sum_{k=1}^{n-1} x_k y_{n-k} + y_k x_{n-k},
 // i.e. Re(conj(v_n) sum v_k v_{n-k}) for v = x - i y (Eq. 42 up to 2 pi c^3).
-template <int KMAX, typename R>
-__device__ __forceinline__ R triad(const R *x, const R *y) {
-    R T = R(0);
+// Packed pairs: with V_m = (x_m, y_m) and S_m = (y_m, x_m),
+//   V_k . V_m (elementwise) = (x_k x_m, y_k y_m)  -> A-part = lo - hi,
+//   V_k . S_m               = (x_k y_m, y_k x_m)  -> B-part = lo + hi,
+// so each symmetric pair (k, n-k) costs two packed FMAs.  The x- and
+// y-products are summed apart and subtracted at the end; every term passes
+// through no more roundings than in a scalar sum over the same pairs, so the
+// rounding-error bound behind the accept guard band holds.
+template <int KMAX>
+__device__ __forceinline__ float triad2(const float *x, const float *y) {
+    f32x2_t V[KMAX], S[KMAX];
+#pragma unroll
+    for (int m = 0; m < KMAX; ++m) {
+        V[m] = pk2(x[m], y[m]);
+        S[m] = pk2(y[m], x[m]);
+    }
+    const f32x2_t two = pk2(2.f, 2.f);
+    float T = 0.f;
 #pragma unroll
     for (int n = 2; n <= KMAX; ++n) {
-        R A = R(0), Bv = R(0);
+        f32x2_t P1 = 0ull, P2 = 0ull;  // 0ull is the pair (+0, +0)
 #pragma unroll
         for (int k = 1; 2 * k < n; ++k) {
-            A = fma(x[k - 1], x[n - k - 1], A);
-            A = fma(-y[k - 1], y[n - k - 1], A);
-            Bv = fma(x[k - 1], y[n - k - 1], Bv);
-            Bv = fma(y[k - 1], x[n - k - 1], Bv);
+            P1 = fma2(V[k - 1], V[n - k - 1], P1);
+            P2 = fma2(V[k - 1], S[n - k - 1], P2);
         }
-        A = A + A;
-        Bv = Bv + Bv;
         if ((n & 1) == 0) {
             const int h = n / 2;
-            A = fma(x[h - 1], x[h - 1], A);
-            A = fma(-y[h - 1], y[h - 1], A);
-            Bv = fma(x[h - 1] + x[h - 1], y[h - 1], Bv);
+            P1 = fma2(P1, two, mul2(V[h - 1], V[h - 1]));
+            P2 = fma2(P2, two, mul2(V[h - 1], S[h - 1]));
+        } else {
+            P1 = mul2(P1, two);
+            P2 = mul2(P2, two);
         }
-        T = fma(x[n - 1], A, T);
-        T = fma(y[n - 1], Bv, T);
+        float a0, a1, b0, b1;
+        upk2(P1, a0, a1);
+        upk2(P2, b0, b1);
+        T = fmaf(x[n - 1], a0 - a1, T);
+        T = fmaf(y[n - 1], b0 + b1, T);
     }
     return T;
 }
@@ -192,14 +300,15 @@ __device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, u
     const float inv2 = 1.f / dr.nrm2;
     f.inv = rsqrtf(dr.nrm2);
     f.S = dr.Sraw * inv2;
-    f.T = triad<KMAX, float>(dr.x, dr.y) * (inv2 * f.inv);
+    f.T = triad2<KMAX>(dr.x, dr.y) * (inv2 * f.inv);
     const float tS = c.cS * f.S;
     const float tH = c.cH * f.T;
     const float tQ = UNIF ? 0.f : c.cQ * logf(dr.zz * inv2);
     f.delta = ((tS + tH) + tQ) - c.logM;
-    f.lnU = logf(u01f(wacc));
+    f.lnU = -0.5f * rho_fast(wacc);
     f.d = f.lnU - f.delta;
-    f.guard = c.ga + c.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(f.lnU) + fabsf(c.logM)) + c.gh;
+    f.guard = fmaf(c.ge * dr.esum, f.inv,
+                   fmaf(c.gq, inv2, c.ga + c.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(f.lnU) + fabsf(c.logM)) + c.gh));
     return f;
 }
 
@@ -241,7 +350,8 @@ __device__ __noinline__ void eval64(const PointConst *P, unsigned long long idx,
     for (int m = 0; m < K; ++m) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)(m / 2), lo, hi, pid), k0, k1);
         const int h = m & 1;
-        const double u1 = u01d(h ? w.z : w.x), u2 = u01d(h ? w.w : w.y);
+        const double u1 = u01d_ext(h ? w.z : w.x, 2u * (uint32_t)m, lo, hi, pid, k0, k1);
+        const double u2 = u01d(h ? w.w : w.y);
         const double rho = -2.0 * log(u1);
         const double rad = sqrt(rho);
         double sn, cs;
@@ -273,7 +383,7 @@ __device__ __noinline__ void eval64(const PointConst *P, unsigned long long idx,
     delta -= P->logM;
     const uint32_t wa = accept_word(lo, hi, pid, K, k0, k1);
     o->delta = delta;
-    o->lnU = log(u01d(wa));
+    o->lnU = log(u01d_ext(wa, 4u * (uint32_t)((K + 1) / 2), lo, hi, pid, k0, k1));
     o->accept = o->lnU < delta;
     o->near = fabs(o->lnU - delta) < 1e-6;
     o->H2 = (float)((double)P->E0 * o->S);
@@ -325,6 +435,44 @@ static __device__ __noinline__ void tally_accepted(float u0, float ha, float hb,
     atomicAdd(&s_q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
 }
 
+// Power spectrum of an accepted draw (mean of s_k = xh_k^2 + xh_{K+k}^2 over
+// the accepted fields, Sec. V.A) into shared fixed-point sums.
+template <int KMAX>
+__device__ __forceinline__ void tally_spectrum(unsigned long long *s_spec, const float *x, const float *y, float inv2,
+                                               int K) {
+    const float sc = inv2 * kSpecScale;
+#pragma unroll
+    for (int m = 0; m < KMAX; ++m)
+        if (m < K) atomicAdd(&s_spec[m], (unsigned long long)__float2ull_rn(fmaf(x[m], x[m], y[m] * y[m]) * sc));
+}
+
+// Outputs of one accepted draw made again with rho_acc: used by the grid form,
+// which keeps no per-mode state, and by the triad form for the few accepted
+// draws holding a radius of the series range.  The draw is evaluated in FP32
+// (T by the double sum), its u(0) statistics and spectrum are tallied, and
+// its record is written when rec is not null (ring full).  Out of line:
+// accepted draws are rare, and the hot loops keep neither this code nor its
+// registers.
+template <int KMAX, bool UNIF>
+__device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long long idx, uint32_t point, uint32_t k0,
+                                           uint32_t k1, const float *sig, const float *act, uint32_t *s_hist,
+                                           uint32_t *s_exc, unsigned long long *s_q, unsigned long long *s_spec,
+                                           unsigned char *rec) {
+    const Scal sc = load_scal(P);
+    Draw<KMAX> dr;
+    draw_fast<KMAX, UNIF, true>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), sc.pid, k0, k1);
+    const float inv2 = 1.f / dr.nrm2;
+    const float inv = rsqrtf(dr.nrm2);
+    const float S = dr.Sraw * inv2;
+    const float T = triad2<KMAX>(dr.x, dr.y) * (inv2 * inv);
+    const float tQ = UNIF ? 0.f : sc.cQ * logf(dr.zz * inv2);
+    const float delta = ((sc.cS * S + sc.cH * T) + tQ) - sc.logM;
+    const float u0 = sc.u0s * dr.u0raw * inv;
+    tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
+    tally_spectrum<KMAX>(s_spec, dr.x, dr.y, inv2, sc.K);
+    if (rec) write_record<KMAX>(rec, idx, point, 0u, sc.E0 * S, sc.h3s * T, u0, delta, dr.x, dr.y, inv, sc.K);
+}
+
 // ---- the persistent sampler ----------------------------------------------
 template <int KMAX, bool UNIF, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
@@ -332,6 +480,7 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ uint32_t s_hist[kHistBins];
     __shared__ uint32_t s_exc[kExcBins];
     __shared__ unsigned long long s_q[4];
+    __shared__ unsigned long long s_spec[KMAX];
     __shared__ uint32_t s_cnt[4];  // accepted, envelope violations, dropped, fallbacks
     __shared__ uint32_t s_maxd;
     __shared__ uint32_t s_chunk;
@@ -339,6 +488,7 @@ __global__ void __launch_bounds__(NT, MINB)
 
     const int tid = threadIdx.x, lane = tid & 31;
     for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
+    for (int e = tid; e < KMAX; e += NT) s_spec[e] = 0ull;
     if (tid < kExcBins) s_exc[tid] = 0;
     if (tid < 4) {
         s_q[tid] = 0ull;
@@ -384,8 +534,10 @@ __global__ void __launch_bounds__(NT, MINB)
             draw_fast<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, k0, k1);
             const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
-            bool defer = valid && fabsf(f.d) < f.guard;
-            if (valid) maxd = fmaxf(maxd, f.delta);
+            // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
+            const bool tail = min(dr.wmin, wa) < kTailBucket;
+            bool defer = valid && (fabsf(f.d) < f.guard || tail);
+            if (valid && !tail) maxd = fmaxf(maxd, f.delta);
 
             // guard band -> FP64 queue
             const unsigned md = __ballot_sync(0xffffffffu, defer);
@@ -422,14 +574,23 @@ __global__ void __launch_bounds__(NT, MINB)
                 }
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
                 if (acc) {
-                    const float u0 = sc.u0s * dr.u0raw * f.inv;
-                    tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
                     const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
-                    if (slot < B.ring_cap) {
-                        write_record<KMAX>(B.ring + slot * B.rec_bytes, idx, (uint32_t)p, 0u, sc.E0 * f.S,
-                                           sc.h3s * f.T, u0, f.delta, dr.x, dr.y, f.inv, sc.K);
-                    } else {
+                    unsigned char *rec = nullptr;
+                    if (slot < B.ring_cap)
+                        rec = B.ring + slot * B.rec_bytes;
+                    else
                         atomicAdd(&s_cnt[2], 1u);
+                    if (dr.rrmax > kSmallRhoRsqrt) {
+                        // a radius of the series range: outputs from rho_acc
+                        emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
+                                                  s_spec, rec);
+                    } else {
+                        const float u0 = sc.u0s * dr.u0raw * f.inv;
+                        tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
+                        tally_spectrum<KMAX>(s_spec, dr.x, dr.y, f.inv * f.inv, sc.K);
+                        if (rec)
+                            write_record<KMAX>(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta,
+                                               dr.x, dr.y, f.inv, sc.K);
                     }
                 }
             }
@@ -453,6 +614,12 @@ __global__ void __launch_bounds__(NT, MINB)
         if (tid < 4 && s_q[tid]) {
             atomicAdd(&st->q[tid], s_q[tid]);
             s_q[tid] = 0ull;
+        }
+        for (int e = tid; e < KMAX; e += NT) {
+            if (s_spec[e]) {
+                atomicAdd(&st->spec[e], s_spec[e]);
+                s_spec[e] = 0ull;
+            }
         }
         if (tid == 0) {
             atomicAdd(&st->n_prop, (unsigned long long)n_here);
@@ -480,6 +647,7 @@ __global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t
         float xh[2 * KMAX];
         eval64<KMAX, UNIF>(P, it.idx, k0, k1, &o, xh);
         atomicAdd(&st->n_refined, 1ull);
+        atomicMax(&st->maxd_key, (unsigned long long)fkey((float)o.delta));
         if (o.near) atomicAdd(&st->n_near, 1ull);
         if (o.delta > 0.0) atomicAdd(&st->n_viol, 1ull);
         if (!o.accept) continue;
@@ -492,6 +660,9 @@ __global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t
         atomicAdd(&st->q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
         atomicAdd(&st->q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
         atomicAdd(&st->q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+        for (int m = 0; m < P->K; ++m)
+            atomicAdd(&st->spec[m],
+                      (unsigned long long)__float2ull_rn(fmaf(xh[m], xh[m], xh[P->K + m] * xh[P->K + m]) * kSpecScale));
         const unsigned long long slot = atomicAdd(B.ring_count, 1ull);
         if (slot < B.ring_cap) {
             const int K = P->K;
@@ -529,7 +700,7 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
     const uint32_t wa = accept_word(lo, hi, sc.pid, K, k0, k1);
     const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
     double *row = out + i * (unsigned long long)(8 + 2 * K);
-    if (fabsf(f.d) < f.guard) {
+    if (fabsf(f.d) < f.guard || min(dr.wmin, wa) < kTailBucket) {
         Out64 o;
         float xh[2 * KMAX];
         eval64<KMAX, UNIF>(P, id, k0, k1, &o, xh);
@@ -544,19 +715,29 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
         for (int m = 0; m < 2 * K; ++m) row[8 + m] = xh[m];
         return;
     }
-    row[0] = f.delta;
-    row[1] = f.lnU;
     row[2] = f.d < 0.f ? 1.0 : 0.0;
     row[3] = 0.0;
-    row[4] = sc.E0 * f.S;
-    row[5] = sc.h3s * f.T;
-    row[6] = sc.u0s * dr.u0raw * f.inv;
-    row[7] = f.S;
+    if (dr.rrmax > kSmallRhoRsqrt) {
+        // a radius of the series range: the values are those of rho_acc, as
+        // the sampler's outputs of an accepted draw would be
+        draw_fast<KMAX, UNIF, true>(dr, P->sigma, P->act, lo, hi, sc.pid, k0, k1);
+    }
+    const float inv2 = 1.f / dr.nrm2;
+    const float inv = rsqrtf(dr.nrm2);
+    const float S = dr.Sraw * inv2;
+    const float T = triad2<KMAX>(dr.x, dr.y) * (inv2 * inv);
+    const float tQ = UNIF ? 0.f : sc.cQ * logf(dr.zz * inv2);
+    row[0] = ((sc.cS * S + sc.cH * T) + tQ) - sc.logM;
+    row[1] = f.lnU;
+    row[4] = sc.E0 * S;
+    row[5] = sc.h3s * T;
+    row[6] = sc.u0s * dr.u0raw * inv;
+    row[7] = S;
 #pragma unroll
     for (int m = 0; m < KMAX; ++m) {
         if (m < K) {
-            row[8 + m] = dr.x[m] * f.inv;
-            row[8 + K + m] = dr.y[m] * f.inv;
+            row[8 + m] = dr.x[m] * inv;
+            row[8 + K + m] = dr.y[m] * inv;
         }
     }
 }

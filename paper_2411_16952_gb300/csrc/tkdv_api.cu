@@ -115,23 +115,15 @@ int build_point(tkdv_sampler *h, int p, std::string &msg) {
     }
     double alpha = 1.0;
     std::vector<double> s2(K, 1.0);
-    if (q.proposal != TKDV_PROPOSAL_UNIFORM) {
-        int rc = tkdv_alpha_star(K, q.beta_p, &alpha);
-        if (rc != TKDV_OK) {
+    {
+        const int rc = proposal_variances(K, q, &alpha, s2.data());
+        if (rc == TKDV_ERR_NO_ALPHA) {
             msg = "point " + std::to_string(p) + ": no root alpha* of F (beta' >= K^2 sum 1/k^2)";
             return rc;
         }
-        const double K3 = (double)K * K * K;
-        for (int k = 1; k <= K; ++k) {
-            s2[k - 1] = 1.0 / (1.0 + alpha * q.beta_p * (double)k * k / K3);  // Eq. (25)
-            if (q.proposal == TKDV_PROPOSAL_LEARNED) {
-                const double c = q.log_var_correction[k - 1];
-                if (!std::isfinite(c)) {
-                    msg = "point " + std::to_string(p) + ": non-finite log-variance correction";
-                    return TKDV_ERR_INVALID_ARG;
-                }
-                s2[k - 1] *= std::exp(c);
-            }
+        if (rc != TKDV_OK) {
+            msg = "point " + std::to_string(p) + ": invalid proposal (non-finite log-variance correction?)";
+            return rc;
         }
     }
     double lm = q.logM;
@@ -151,46 +143,7 @@ int build_point(tkdv_sampler *h, int p, std::string &msg) {
     h->sigma2[p] = s2;
 
     PointConst c;
-    std::memset(&c, 0, sizeof(c));
-    for (int k = 0; k < kKMax; ++k) {
-        const bool on = k < K;
-        c.sigma[k] = on ? (float)std::sqrt(s2[k]) : 0.f;
-        c.sigma_d[k] = on ? std::sqrt(s2[k]) : 0.0;
-        c.act[k] = on ? 1.f : 0.f;
-    }
-    const double K2 = (double)K * K;
-    const double cc = std::sqrt(q.E0 / (2.0 * M_PI));
-    const double h3s = 2.0 * M_PI * cc * cc * cc;
-    c.cS_d = -q.beta_p / K2;                         // Eq. (43), H2 = E0 S
-    c.cH_d = q.beta_p * q.r / (q.E0 * K2) * h3s;     // Eq. (43), H3 = h3s T
-    c.cQ_d = q.proposal == TKDV_PROPOSAL_UNIFORM ? 0.0 : (double)K;  // Eq. (40) / (37)
-    c.logM = lm;
-    c.cS = (float)c.cS_d;
-    c.cH = (float)c.cH_d;
-    c.cQ = (float)c.cQ_d;
-    c.logM_f = (float)lm;
-    c.u0s = (float)(2.0 * cc);
-    c.h3s = (float)h3s;
-    c.E0 = (float)q.E0;
-    const double ucap = std::sqrt(2.0 * K * q.E0 / M_PI);
-    c.hist_a = (float)(kHistBins / (2.0 * ucap));
-    c.hist_b = (float)(kHistBins / 2);
-    c.exc_a = (float)(1.0 / (0.25 * std::sqrt(q.E0 / M_PI)));
-    // Guard band of the FP32 decision.  The FP32 value of log f/(Mg) carries
-    // the rounding of ~2K+16 chained operations on each term; T additionally
-    // sums O(K) products per mode with |T| <= sqrt(K) on the sphere.  The band
-    // is eight times that bound; proposals inside it are decided in FP64.
-    const double gam = 8.0 * (2.0 * K + 16.0) * std::ldexp(1.0, -24);
-    c.guard_abs = (float)(1e-6 + gam * std::fabs(c.cQ_d));
-    c.guard_rel = (float)gam;
-    c.guard_h = (float)(gam * std::fabs(c.cH_d) * std::sqrt((double)K));
-    if (h->opt.h3_mode == TKDV_H3_GRID_BF16X3) {
-        // BF16 hi/lo x3: |dU_j| <= 2^-15.4 sqrt(2K) |x| per grid value, so with
-        // sum_j U_j^2 = (N/2)|x|^2 the error of T is below 2^-14.4 sqrt(2K)
-        c.guard_h += (float)(std::ldexp(1.0, -14) * std::sqrt(2.0 * K) * std::fabs(c.cH_d));
-    }
-    c.point_id = q.point_id;
-    c.K = K;
+    fill_point_const(K, q, s2.data(), lm, h->opt.h3_mode == TKDV_H3_GRID_BF16X3, c);
     h->pc[p] = c;
     return TKDV_OK;
 }
@@ -663,6 +616,7 @@ int sampler_stats(tkdv_sampler *h, tkdv_stats *out, int n_out) {
             for (int e = i + 1; e < kExcBins; ++e) t += s.exc[e];
             o.exceed[i] = t;
         }
+        for (int m = 0; m < h->K && m < TKDV_KMAX; ++m) o.spectrum[m] = (double)s.spec[m] / (double)kSpecScale;
     }
     return rc;
 }
@@ -677,6 +631,39 @@ int sampler_samples(tkdv_sampler *h, void *dst, int dst_on_device, uint64_t max_
     if (n) CK(cudaMemcpy(dst, h->d_ring, n * h->rec_bytes, dst_on_device ? cudaMemcpyDeviceToDevice
                                                                            : cudaMemcpyDeviceToHost));
     *n_out = n;
+    return TKDV_OK;
+}
+
+int sampler_field_maxima(tkdv_sampler *h, uint64_t max_records, double *umax, int32_t *jmax, uint64_t *n_out) {
+    if (!h || !n_out || (max_records && !umax)) return TKDV_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long cnt = 0;
+    CK(cudaMemcpy(&cnt, h->d_ring_count, 8, cudaMemcpyDeviceToHost));
+    unsigned long long n = std::min<unsigned long long>(cnt, h->dev.ring_cap);
+    n = std::min<unsigned long long>(n, max_records);
+    *n_out = n;
+    if (!n) return TKDV_OK;
+    float *d_u = nullptr;
+    int *d_j = nullptr;
+    if (cudaMalloc(&d_u, 4 * n) != cudaSuccess) return fail(h, TKDV_ERR_OOM, "field maxima: out of device memory");
+    if (cudaMalloc(&d_j, 4 * n) != cudaSuccess) {
+        cudaFree(d_u);
+        return fail(h, TKDV_ERR_OOM, "field maxima: out of device memory");
+    }
+    cudaError_t e = launch_field_max((const unsigned char *)h->d_ring, h->rec_bytes, n, h->K,
+                                     (const PointConst *)h->d_pts, d_u, d_j, h->stream);
+    std::vector<float> hu(n);
+    std::vector<int> hj(n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(hu.data(), d_u, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hj.data(), d_j, 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(d_u);
+    cudaFree(d_j);
+    if (e != cudaSuccess) return fail(h, TKDV_ERR_CUDA, cudaGetErrorString(e));
+    for (unsigned long long i = 0; i < n; ++i) {
+        umax[i] = hu[i];
+        if (jmax) jmax[i] = hj[i];
+    }
     return TKDV_OK;
 }
 

@@ -5,6 +5,10 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
+#include "tkdv.h"
+
 namespace tkdv {
 
 constexpr int kKMax = 64;
@@ -18,6 +22,12 @@ constexpr float kQ1 = 268435456.0f;  // 2^28
 constexpr float kQ2 = 16777216.0f;   // 2^24
 constexpr float kQ3 = 1048576.0f;    // 2^20
 constexpr float kQ4 = 65536.0f;      // 2^16
+// Fixed-point scale of the per-mode spectrum sums (s_k <= 1: 2^36 accepts per point fit).
+constexpr float kSpecScale = 268435456.0f;  // 2^28
+// Error bound of the FP32 radius -2 ln u on the fast path (rho_fast):
+// |rho_fast - rho| <= kRhoAbsErr + kRhoRelErr * rho for every value of the map.
+constexpr double kRhoAbsErr = 0x1p-21;
+constexpr double kRhoRelErr = 0x1p-21;
 
 // Per-point constants, built on the host from the precompute (alpha*, sigma_k,
 // log M) and read by every proposal of that point.
@@ -37,10 +47,10 @@ struct PointConst {
     float E0;
     float hist_a, hist_b;  // histogram bin = floor(u0 * hist_a + hist_b)
     float exc_a;           // exceed bin = ceil(u0 * exc_a) for u0 > 0
-    float guard_abs, guard_rel, guard_h;  // FP32 decision guard (see sampler_impl.cuh)
+    float guard_abs, guard_rel, guard_h;  // FP32 decision guard (point_table.cpp)
     uint32_t point_id;
     int K;
-    int pad[2];
+    float guard_e, guard_q;  // per-draw guard terms for the radius error (point_table.cpp)
 };
 
 // Statistics of one point on the device: only integers, so that the result
@@ -53,6 +63,7 @@ struct StatBlock {
     unsigned long long exc[kExcBins];
     unsigned long long n_fallback;  // guard-band proposals decided in FP32 (queue full)
     unsigned long long pad[2];
+    unsigned long long spec[kKMax];  // sum of round(s_k * kSpecScale), s_k = xh_k^2 + xh_{K+k}^2
 };
 
 struct RefineItem {
@@ -126,5 +137,14 @@ inline size_t record_bytes(int K) {
     size_t b = 32 + 8 * (size_t)K;
     return (b + 15) & ~(size_t)15;
 }
+
+// Host: proposal variances sigma_k^2 (Eq. 25, learned corrections applied)
+// and alpha*; returns a TKDV_ status.  s2 has K entries.
+int proposal_variances(int K, const tkdv_point &q, double *alpha, double *s2);
+// Host: the kernels' constant table of one point (coefficients, scales, guard).
+void fill_point_const(int K, const tkdv_point &q, const double *s2, double logM, bool grid, PointConst &c);
+// Largest displacement of n kept records on the 2K-point grid (fields.cu).
+cudaError_t launch_field_max(const unsigned char *ring, unsigned long long rec_bytes, unsigned long long n, int K,
+                             const PointConst *pts, float *umax, int *jmax, cudaStream_t st);
 
 }  // namespace tkdv

@@ -49,7 +49,7 @@ std::once_flag g_once[kMaxDevices];
 unsigned char *g_scratch_ptr[kMaxDevices];
 cudaError_t g_scratch_err[kMaxDevices];
 
-// Same per-point table as the handle API builds (see tkdv_api.cu), written
+// Same per-point table as the handle API builds (point_table.cpp), built
 // without any allocation.
 int fill_point(int K, const tkdv_point &q, PointConst &c, double &alpha) {
     if (!(q.E0 > 0) || !std::isfinite(q.E0)) return TKDV_ERR_INVALID_ARG;
@@ -60,53 +60,10 @@ int fill_point(int K, const tkdv_point &q, PointConst &c, double &alpha) {
         return TKDV_ERR_INVALID_ARG;
     if (q.proposal == TKDV_PROPOSAL_LEARNED && !q.log_var_correction)
         return TKDV_ERR_INVALID_ARG;
-    alpha = 1.0;
     double s2[kKMax];
-    for (int k = 0; k < kKMax; ++k) s2[k] = 1.0;
-    if (q.proposal != TKDV_PROPOSAL_UNIFORM) {
-        int rc = tkdv_alpha_star(K, q.beta_p, &alpha);
-        if (rc != TKDV_OK) return rc;
-        const double K3 = (double)K * K * K;
-        for (int k = 1; k <= K; ++k) {
-            s2[k - 1] = 1.0 / (1.0 + alpha * q.beta_p * (double)k * k / K3);
-            if (q.proposal == TKDV_PROPOSAL_LEARNED) {
-                if (!std::isfinite(q.log_var_correction[k - 1]))
-                    return TKDV_ERR_INVALID_ARG;
-                s2[k - 1] *= std::exp(q.log_var_correction[k - 1]);
-            }
-        }
-    }
-    std::memset(&c, 0, sizeof(c));
-    for (int k = 0; k < kKMax; ++k) {
-        const bool on = k < K;
-        c.sigma[k] = on ? (float)std::sqrt(s2[k]) : 0.f;
-        c.sigma_d[k] = on ? std::sqrt(s2[k]) : 0.0;
-        c.act[k] = on ? 1.f : 0.f;
-    }
-    const double K2 = (double)K * K;
-    const double cc = std::sqrt(q.E0 / (2.0 * M_PI));
-    const double h3s = 2.0 * M_PI * cc * cc * cc;
-    c.cS_d = -q.beta_p / K2;
-    c.cH_d = q.beta_p * q.r / (q.E0 * K2) * h3s;
-    c.cQ_d = q.proposal == TKDV_PROPOSAL_UNIFORM ? 0.0 : (double)K;
-    c.logM = q.logM;
-    c.cS = (float)c.cS_d;
-    c.cH = (float)c.cH_d;
-    c.cQ = (float)c.cQ_d;
-    c.logM_f = (float)q.logM;
-    c.u0s = (float)(2.0 * cc);
-    c.h3s = (float)h3s;
-    c.E0 = (float)q.E0;
-    const double ucap = std::sqrt(2.0 * K * q.E0 / M_PI);
-    c.hist_a = (float)(kHistBins / (2.0 * ucap));
-    c.hist_b = (float)(kHistBins / 2);
-    c.exc_a = (float)(1.0 / (0.25 * std::sqrt(q.E0 / M_PI)));
-    const double gam = 8.0 * (2.0 * K + 16.0) * std::ldexp(1.0, -24);
-    c.guard_abs = (float)(1e-6 + gam * std::fabs(c.cQ_d));
-    c.guard_rel = (float)gam;
-    c.guard_h = (float)(gam * std::fabs(c.cH_d) * std::sqrt((double)K));
-    c.point_id = q.point_id;
-    c.K = K;
+    const int rc = proposal_variances(K, q, &alpha, s2);
+    if (rc != TKDV_OK) return rc;
+    fill_point_const(K, q, s2, q.logM, false, c);
     return TKDV_OK;
 }
 
@@ -254,6 +211,7 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
             for (int j = i + 1; j < kExcBins; ++j) t += sb.exc[j];
             o.exceed[i] = t;
         }
+        for (int m = 0; m < K && m < TKDV_KMAX; ++m) o.spectrum[m] = (double)sb.spec[m] / (double)kSpecScale;
     }
     if (status & kStatusDeadline) return TKDV_ERR_TIMEOUT;
     return TKDV_OK;

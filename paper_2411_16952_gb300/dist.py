@@ -31,14 +31,15 @@ def rank_point_id(rank: int, point: int, n_points: int) -> int:
 def merge_stats(stats, group=None):
     """Sum per-point statistics over ranks (torch.distributed all-reduce).
     stats: list of dicts as returned by Sampler.stats(); returns merged dicts
-    with integer counters, histogram, exceedance counts and power sums added
-    and max_delta maximised."""
+    with integer counters, histogram, exceedance counts, power sums and the
+    spectrum sums added and max_delta maximised."""
     import torch
     import torch.distributed as dist
     P = len(stats)
     ints = np.array([[s[k] for k in INT_KEYS] + list(s["hist"]) + list(s["exceed"]) for s in stats],
                     dtype=np.int64)
-    sums = np.array([list(s["sum_u0"]) for s in stats], dtype=np.float64)
+    sums = np.array([list(s["sum_u0"]) + list(s.get("spectrum", np.zeros(64))) for s in stats],
+                    dtype=np.float64)
     mx = np.array([s["max_delta"] for s in stats], dtype=np.float64)
     ti, ts, tm = torch.from_numpy(ints), torch.from_numpy(sums), torch.from_numpy(mx)
     dist.all_reduce(ti, group=group)
@@ -51,7 +52,8 @@ def merge_stats(stats, group=None):
         d = {k: int(ints[p, i]) for i, k in enumerate(INT_KEYS)}
         d["hist"] = ints[p, len(INT_KEYS):len(INT_KEYS) + nh].astype(np.uint64)
         d["exceed"] = ints[p, len(INT_KEYS) + nh:].astype(np.uint64)
-        d["sum_u0"] = sums[p]
+        d["sum_u0"] = sums[p, :4]
+        d["spectrum"] = sums[p, 4:]
         d["max_delta"] = float(mx[p])
         out.append(d)
     return out

@@ -21,7 +21,8 @@ def _free_port():
 def _as_lib_stats(st):
     return {"n_proposals": st["n_prop"], "n_accepted": st["n_acc"], "n_near_threshold": st["n_near"],
             "n_refined": 0, "n_envelope_violations": st["n_viol"], "n_dropped": 0, "n_fallback": 0,
-            "hist": st["hist"], "exceed": st["exceed"], "sum_u0": st["sum_u0"], "max_delta": st["max_delta"]}
+            "hist": st["hist"], "exceed": st["exceed"], "sum_u0": st["sum_u0"], "max_delta": st["max_delta"],
+            "spectrum": np.concatenate([st["spectrum"], np.zeros(64 - len(st["spectrum"]))])}
 
 
 def _worker(rank, world, port, q):
@@ -66,6 +67,7 @@ def test_two_ranks_merge_to_one_run():
     assert np.array_equal(merged[0]["hist"], one["hist"])
     assert np.array_equal(merged[0]["exceed"], one["exceed"])
     assert np.allclose(merged[0]["sum_u0"], one["sum_u0"], rtol=1e-12)
+    assert np.allclose(merged[0]["spectrum"], one["spectrum"], rtol=1e-12, atol=1e-9)
     assert merged[0]["max_delta"] == one["max_delta"]
     # rank-specific streams: point ids 1 and 3 are different draws
     assert merged[1]["n_proposals"] == 100_000

@@ -64,8 +64,13 @@ def test_grid_trace_matches_oracle(T, K, N, E0, bp, r):
     st = S.stats()[0]
     S.close()
     tr = tr.cpu().numpy().reshape(n, 2).astype(np.float64)
+    # draws with a word in the lowest bucket of the uniform map (about 2K + 1
+    # in 2^23) are traced as NaN: they are decided in FP64 with the refined tail
+    keep = ~np.isnan(tr[:, 0])
+    assert np.sum(~keep) <= 4
+    tr = tr[keep]
     pt = O.make_point(K, E0, bp, r, O.PAPER, logM=lm)
-    o = O.replay(pt, seed, 2, np.arange(i0, i0 + n, dtype=np.uint64))
+    o = O.replay(pt, seed, 2, np.arange(i0, i0 + n, dtype=np.uint64)[keep])
     h3s = 2 * math.pi * (E0 / (2 * math.pi)) ** 1.5
     H3g = h3s * tr[:, 1]
     scale = np.abs(o["H2"]) + np.abs(r * o["H3"])
@@ -106,6 +111,10 @@ def test_grid_accepts_what_triad_accepts(T, K, N, bp, r):
     assert sg[0]["n_near_threshold"] == st[0]["n_near_threshold"]
     # moments: identical draws; u0 rounded in FP32 by two differently compiled kernels
     assert np.allclose(sg[0]["sum_u0"], st[0]["sum_u0"], rtol=1e-6, atol=1e-5)
+    # power spectrum of the accepted fields: same draws, both sum to the accept count
+    assert np.allclose(sg[0]["spectrum"], st[0]["spectrum"], rtol=1e-6, atol=1e-5)
+    assert abs(sg[0]["spectrum"].sum() - sg[0]["n_accepted"]) <= 1e-5 * sg[0]["n_accepted"] + 1e-3
+    assert np.all(sg[0]["spectrum"][K:] == 0)
     # oracle check of a sample of the grid form's records
     pt = O.make_point(K, 1.0, bp, r, O.PAPER, logM=lm)
     sel = np.arange(0, len(rg["idx"]), max(1, len(rg["idx"]) // 2000))

@@ -1,4 +1,4 @@
-"""Naive (uniform-proposal) rows of Table 2, which the paper could not finish.
+"""Naive (uniform-proposal) rows of Table 2.
 
 For mean-zero log-variance changes and for the uniform proposal alike, the
 acceptance of a rejection sampler with proposal density g = prod w_k Q^-K
@@ -10,7 +10,9 @@ exp(sum_k ln w_k + log M_uniform - log M_paper), with no Monte Carlo.
 This test measures the uniform proposal's acceptance on the GPU at K = 32
 rows where the printed improvement and the identity disagree most, and
 checks the measurement against the identity (the printed value is reported
-alongside).  Both envelopes come from the library's search.
+alongside).  Both envelopes come from the library's search.  At these
+acceptances a large share of the accepted draws have log f/(Mg) below
+ln 2^-24, so the rows also check the refined tail of the uniform map.
 """
 import json
 import math
@@ -35,8 +37,15 @@ def T():
     return T
 
 
-@pytest.mark.parametrize("bp,r,log2n", [(20.0, 150.0, 28), (40.0, 150.0, 32), (40.0, 225.0, 34)])
-def test_uniform_acceptance_matches_identity(T, bp, r, log2n):
+ROWS = [(20.0, 150.0, 28, 26), (40.0, 150.0, 32, 26), (40.0, 225.0, 34, 28), (40.0, 300.0, 36, 30)]
+# An asterisked row of Table 2 (uniform acceptance about 7.5e-12: 2^40
+# proposals, a few minutes, give about 8 accepts); run with TKDV_LONG_TESTS=1.
+LONG_ROWS = [(40.0, 450.0, 40, 34)]
+long_only = pytest.mark.skipif(not os.environ.get("TKDV_LONG_TESTS"), reason="set TKDV_LONG_TESTS=1")
+
+
+@pytest.mark.parametrize("bp,r,log2n,log2p", ROWS + [pytest.param(*x, marks=long_only) for x in LONG_ROWS])
+def test_uniform_acceptance_matches_identity(T, bp, r, log2n, log2p):
     K, E0 = 32, 1.0
     row = [x for x in GOLD["table2_K32"]["rows"] if x[0] == bp and x[1] == r][0]
     acc_paper_printed, imp_printed = row[3], row[4]
@@ -48,7 +57,7 @@ def test_uniform_acceptance_matches_identity(T, bp, r, log2n):
     improvement = math.exp(np.sum(np.log(1.0 / s2)) + lm_u - lm_p)
     # measured: both proposals on the GPU
     n_u = 1 << log2n
-    n_p = 1 << 26
+    n_p = 1 << log2p
     Su = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_UNIFORM, point_id=1)], sample_capacity=16)
     Sp = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=2)], sample_capacity=16)
     Su.autotune(1 << 22)
@@ -59,7 +68,7 @@ def test_uniform_acceptance_matches_identity(T, bp, r, log2n):
     Sp.close()
     assert su["n_envelope_violations"] == 0 and sp["n_envelope_violations"] == 0
     acc_u, acc_p = su["n_accepted"] / n_u, sp["n_accepted"] / n_p
-    assert su["n_accepted"] >= 100
+    assert su["n_accepted"] >= (1 if log2n >= 40 else 100)
     pred_u = acc_p / improvement
     se = math.sqrt(pred_u / n_u) + pred_u * math.sqrt((1 - acc_p) / (acc_p * n_p))
     assert abs(acc_u - pred_u) <= 4 * se, (acc_u, pred_u, se)

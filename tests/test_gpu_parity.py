@@ -108,6 +108,9 @@ def test_small_k16_full_replay(T, prop):
     if excused == 0:
         for q in range(4):
             assert abs(st["sum_u0"][q] - ost["sum_u0"][q]) <= 2e-6 * (1 + abs(ost["sum_u0"][q])) + 1e-6 * total
+        # power spectrum (Sec. V.A): FP32 s_k per accept, each rounded to 2^-28
+        spec_tol = 2e-6 * ost["spectrum"] + total * 2.0**-28 + 1e-9
+        assert np.all(np.abs(st["spectrum"][:K] - ost["spectrum"]) <= spec_tol)
         edges = np.linspace(st["hist_lo"], st["hist_hi"], 257)
         near_edge = np.sum(np.min(np.abs(orec["u0"][:, None] - edges[None, :]), axis=1) < 1e-5)
         assert int(np.sum(np.abs(st["hist"].astype(np.int64) - ost["hist"].astype(np.int64)))) <= 2 * near_edge
