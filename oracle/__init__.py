@@ -65,6 +65,13 @@ class Stats(C.Structure):
                 ("exceed", C.c_uint64 * N_EXCEED)]
 
 
+class SirStats(C.Structure):
+    _fields_ = [("n_prop", C.c_uint64), ("n_kept", C.c_uint64), ("n_copies", C.c_uint64),
+                ("sum_w", C.c_double), ("sum_w2", C.c_double), ("sum_wS", C.c_double),
+                ("sum_w_u0", C.c_double * 4), ("sum_nS", C.c_double), ("sum_n_u0", C.c_double * 4),
+                ("spectrum", C.c_double * KMAX)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -110,6 +117,14 @@ def lib():
             L.orc_run_accepted.argtypes = [C.POINTER(Point), C.c_uint64, C.c_uint32, C.c_uint64,
                                            C.c_uint64, C.c_int, C.POINTER(Rec), C.c_uint64]
             L.orc_run_accepted.restype = C.c_uint64
+            L.orc_poisson_tail.argtypes = [C.c_double, C.c_int]
+            L.orc_poisson_tail.restype = C.c_double
+            L.orc_poisson_count.argtypes = [C.c_double, C.c_double]
+            L.orc_poisson_count.restype = C.c_int
+            L.orc_run_sir.argtypes = [C.POINTER(Point), C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64, C.c_double,
+                                      C.c_int, C.POINTER(SirStats), C.POINTER(Rec), C.POINTER(C.c_uint32),
+                                      C.c_uint64]
+            L.orc_run_sir.restype = C.c_uint64
             _lib = L
     return _lib
 
@@ -290,3 +305,31 @@ def moments(n, sums):
     c3 = m3 - 3 * m1 * m2 + 2 * m1 ** 3
     c4 = m4 - 4 * m1 * m3 + 6 * m1 * m1 * m2 - 3 * m1 ** 4
     return dict(mean=m1, var=var, skew=c3 / var ** 1.5, kurt=c4 / var ** 2)
+
+
+# ------------------------------------------------------------------ SIR
+def poisson_tail(lam, k):
+    """P(N >= k), N ~ Poisson(lam)."""
+    return lib().orc_poisson_tail(float(lam), int(k))
+
+
+def poisson_count(lam, u):
+    """#{k >= 1 : u < P(N >= k)}: a Poisson(lam) count by inversion of u."""
+    return lib().orc_poisson_count(float(lam), float(u))
+
+
+def run_sir(pt, seed, point_id, idx0, n, c, cap=1 << 16, nthreads=None):
+    """SIR with Poisson copy numbers n_i ~ Poisson(c exp(Delta_i)) over proposals
+    idx0 .. idx0+n-1: returns (statistics dict, kept records dict with "copies")."""
+    st = SirStats()
+    recs = (Rec * max(cap, 1))()
+    cnt = (C.c_uint32 * max(cap, 1))()
+    nt = nthreads or os.cpu_count() or 1
+    total = lib().orc_run_sir(C.byref(pt), seed, point_id, idx0, n, float(c), nt, C.byref(st), recs, cnt, cap)
+    got = min(total, cap)
+    d = {"n_prop": st.n_prop, "n_kept": st.n_kept, "n_copies": st.n_copies, "sum_w": st.sum_w,
+         "sum_w2": st.sum_w2, "sum_wS": st.sum_wS, "sum_w_u0": np.array(st.sum_w_u0[:]), "sum_nS": st.sum_nS,
+         "sum_n_u0": np.array(st.sum_n_u0[:]), "spectrum": np.array(st.spectrum[:pt.K])}
+    kept = _recs_to_dict(recs, got, pt.K)
+    kept["copies"] = np.array(cnt[:got], dtype=np.int64)
+    return d, kept

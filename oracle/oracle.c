@@ -753,3 +753,160 @@ uint64_t orc_run_accepted(const orc_point *pt, uint64_t seed, uint32_t point_id,
     free(jobs);
     return total;
 }
+
+/* ---------------------------------------------------------------------------
+ * Sampling-importance resampling (SIR) with the same proposal.  Sec. IV.B
+ * names SIR with g as the alternative use of the proposal: every draw
+ * carries the importance weight f/g, proportional to exp(Delta), Delta =
+ * log f/(Mg) the quantity of the rejection test (log M only shifts it), and
+ * the resampled set keeps each draw in proportion to its weight.  Here draw
+ * i gets an independent Poisson number of copies n_i ~ Poisson(c exp(Delta_i)),
+ * drawn by inversion of the draw's accept uniform U_i:
+ * n_i = #{k >= 1 : U_i < P(N >= k)}.  Conditioned on their total the n_i are
+ * multinomial with probabilities exp(Delta_i) / sum_j exp(Delta_j), the
+ * classical SIR draw; c sets the expected total.
+ * ------------------------------------------------------------------------- */
+
+/* P(N >= k) for N ~ Poisson(lambda), k >= 1: the tail series
+ * e^-l l^k/k! sum_i l^i k!/(k+i)! for lambda <= k + 1 (no cancellation),
+ * else 1 - e^-l sum_{j<k} l^j/j!. */
+double orc_poisson_tail(double lambda, int k)
+{
+    if (lambda <= 0.0)
+        return 0.0;
+    if (lambda <= k + 1.0) {
+        double lead = exp(-lambda + k * log(lambda) - lgamma(k + 1.0));
+        double term = 1.0, sum = 1.0;
+        for (int i = 1; i < 200; ++i) {
+            term *= lambda / (k + i);
+            sum += term;
+            if (term < 1e-18 * sum)
+                break;
+        }
+        return lead * sum;
+    }
+    double p = exp(-lambda), s = p;
+    for (int j = 1; j < k; ++j) {
+        p *= lambda / j;
+        s += p;
+    }
+    return 1.0 - s;
+}
+
+/* n = #{k >= 1 : u < P(N >= k)} for N ~ Poisson(lambda). */
+int orc_poisson_count(double lambda, double u)
+{
+    int n = 0;
+    while (n < 100000 && u < orc_poisson_tail(lambda, n + 1))
+        ++n;
+    return n;
+}
+
+/* One proposal of the SIR run: its weight terms and its number of copies. */
+static void orc_sir_add(orc_sir_stats *st, const orc_point *pt, const orc_rec *rc, double c, orc_rec *kept,
+                        uint32_t *kept_n, uint64_t cap, uint64_t *n_kept)
+{
+    st->n_prop += 1;
+    double w = exp(rc->delta);
+    st->sum_w += w;
+    st->sum_w2 += w * w;
+    st->sum_wS += w * rc->S;
+    double p = w;
+    for (int q = 0; q < 4; ++q) {
+        p *= rc->u0;
+        st->sum_w_u0[q] += p;
+    }
+    int n = orc_poisson_count(c * w, exp(rc->lnU));
+    if (n == 0) return;
+    if (*n_kept < cap) {
+        kept[*n_kept] = *rc;
+        kept_n[*n_kept] = (uint32_t)n;
+    }
+    *n_kept += 1;
+    st->n_kept += 1;
+    st->n_copies += (uint64_t)n;
+    st->sum_nS += n * rc->S;
+    p = (double)n;
+    for (int q = 0; q < 4; ++q) {
+        p *= rc->u0;
+        st->sum_n_u0[q] += p;
+    }
+    for (int k = 1; k <= pt->K; ++k)
+        st->spectrum[k - 1] += n * (rc->xhat[k - 1] * rc->xhat[k - 1] + rc->xhat[pt->K + k - 1] * rc->xhat[pt->K + k - 1]);
+}
+
+typedef struct {
+    const orc_point *pt;
+    uint64_t seed, idx0, begin, end, cap, n_kept;
+    uint32_t point_id;
+    double c;
+    orc_sir_stats st;
+    orc_rec *kept;
+    uint32_t *kept_n;
+} orc_sir_job;
+
+static void *orc_sir_worker(void *arg)
+{
+    orc_sir_job *jb = (orc_sir_job *)arg;
+    orc_rec rc;
+    for (uint64_t i = jb->begin; i < jb->end; ++i) {
+        orc_one(jb->pt, jb->seed, jb->point_id, jb->idx0 + i, &rc);
+        orc_sir_add(&jb->st, jb->pt, &rc, jb->c, jb->kept, jb->kept_n, jb->cap, &jb->n_kept);
+    }
+    return NULL;
+}
+
+uint64_t orc_run_sir(const orc_point *pt, uint64_t seed, uint32_t point_id, uint64_t idx0, uint64_t n, double c,
+                     int nthreads, orc_sir_stats *out, orc_rec *kept, uint32_t *kept_n, uint64_t cap)
+{
+    if (nthreads <= 0) nthreads = 1;
+    if ((uint64_t)nthreads > n && n > 0) nthreads = (int)n;
+    if (n == 0) nthreads = 1;
+    orc_sir_job *jobs = (orc_sir_job *)calloc((size_t)nthreads, sizeof(orc_sir_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) {
+        orc_sir_job *jb = &jobs[t];
+        jb->pt = pt;
+        jb->seed = seed;
+        jb->point_id = point_id;
+        jb->idx0 = idx0;
+        jb->c = c;
+        jb->begin = n * (uint64_t)t / (uint64_t)nthreads;
+        jb->end = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
+        jb->cap = cap;
+        jb->kept = (orc_rec *)malloc(sizeof(orc_rec) * (size_t)(cap ? cap : 1));
+        jb->kept_n = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cap ? cap : 1));
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, orc_sir_worker, &jobs[t]);
+    orc_sir_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    memset(out, 0, sizeof(*out));
+    uint64_t total = 0, w = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        orc_sir_stats *s = &jobs[t].st;
+        out->n_prop += s->n_prop;
+        out->n_kept += s->n_kept;
+        out->n_copies += s->n_copies;
+        out->sum_w += s->sum_w;
+        out->sum_w2 += s->sum_w2;
+        out->sum_wS += s->sum_wS;
+        out->sum_nS += s->sum_nS;
+        for (int q = 0; q < 4; ++q) {
+            out->sum_w_u0[q] += s->sum_w_u0[q];
+            out->sum_n_u0[q] += s->sum_n_u0[q];
+        }
+        for (int k = 0; k < ORC_KMAX; ++k) out->spectrum[k] += s->spectrum[k];
+        uint64_t got = jobs[t].n_kept < cap ? jobs[t].n_kept : cap;
+        for (uint64_t i = 0; i < got && w < cap; ++i) {
+            kept[w] = jobs[t].kept[i];
+            kept_n[w] = jobs[t].kept_n[i];
+            ++w;
+        }
+        total += jobs[t].n_kept;
+        free(jobs[t].kept);
+        free(jobs[t].kept_n);
+    }
+    free(jobs);
+    free(th);
+    return total;
+}

@@ -108,6 +108,27 @@ int orc_run_stats(const orc_point *pt, uint64_t seed, uint32_t point_id, uint64_
 uint64_t orc_run_accepted(const orc_point *pt, uint64_t seed, uint32_t point_id, uint64_t idx0,
                           uint64_t n, int nthreads, orc_rec *out, uint64_t cap);
 
+/* Sampling-importance resampling with the same proposal (see oracle.c). */
+typedef struct {
+    uint64_t n_prop;     /* proposals */
+    uint64_t n_kept;     /* proposals with at least one copy */
+    uint64_t n_copies;   /* resampled fields, counted with multiplicity */
+    double sum_w, sum_w2;          /* sum of the weights exp(Delta) and of their squares */
+    double sum_wS, sum_w_u0[4];    /* weighted sums of S and of u0^p (importance sampling) */
+    double sum_nS, sum_n_u0[4];    /* the same over the resampled fields */
+    double spectrum[ORC_KMAX];     /* sum over resampled fields of s_k */
+} orc_sir_stats;
+
+/* P(N >= k) for N ~ Poisson(lambda), k >= 1. */
+double orc_poisson_tail(double lambda, int k);
+/* #{k >= 1 : u < P(N >= k)}: a Poisson(lambda) count by inversion of u. */
+int orc_poisson_count(double lambda, double u);
+/* SIR over proposals idx0 .. idx0+n-1 with c copies per unit exp(Delta):
+ * statistics, and the kept proposals (records and copy counts, first cap, in
+ * index order); returns the number of kept proposals. */
+uint64_t orc_run_sir(const orc_point *pt, uint64_t seed, uint32_t point_id, uint64_t idx0, uint64_t n, double c,
+                     int nthreads, orc_sir_stats *out, orc_rec *kept, uint32_t *kept_n, uint64_t cap);
+
 #ifdef __cplusplus
 }
 #endif
