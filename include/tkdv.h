@@ -98,6 +98,10 @@ typedef struct {
        corrections c_k (k = 1..K); sigma_k^2 = sigma_k^2(paper) * exp(c_k).
        Copied at create time; may be NULL for the other proposals. */
     const double *log_var_correction;
+    /* SIR runs only (tkdv_options.sir): expected copies per unit of
+       exp(log f/(Mg)); a proposal is kept n ~ Poisson(sir_c exp(log f/(Mg)))
+       times.  > 0; ignored by rejection runs. */
+    double sir_c;
 } tkdv_point;
 
 /* Options shared by all points of one handle. */
@@ -111,6 +115,11 @@ typedef struct {
     int use_graph;            /* 1: launch each run as one CUDA graph (default), 0: plain launches */
     int ctas_per_sm;          /* 0: occupancy maximum; else persistent CTAs per SM */
     int threads_per_cta;      /* 0: default (256); 128 or 256 */
+    int sir;                  /* 0: rejection sampling (Sec. IV.B); 1: sampling-importance resampling with
+                                 the same proposal (named in Sec. IV.B): every proposal carries the weight
+                                 exp(log f/(Mg)) and is kept n ~ Poisson(sir_c exp(log f/(Mg))) times, n drawn
+                                 by inversion of its accept uniform, n = #{k >= 1 : U < P(N >= k)}; given
+                                 their total the copies are the multinomial SIR draw.  Triad form only. */
 } tkdv_options;
 
 /* Statistics of one point, accumulated over runs until sampler_reset().
@@ -135,6 +144,15 @@ typedef struct {
     double spectrum[TKDV_KMAX];     /* sum over accepted of s_k = xhat_k^2 + xhat_{K+k}^2 = |u_k|^2 2pi/E0,
                                        k = 1..K (0 beyond K); spectrum / n_accepted is the mean power
                                        spectrum of Sec. V.A.  Each term is rounded to 2^-28. */
+    /* SIR runs: n_accepted, the histogram, moments, exceedances and spectrum
+       count every copy; n_kept counts the proposals with at least one copy.
+       The importance-sampling sums run over all proposals, with w =
+       exp(log f/(Mg)) from the FP32 path: E_f[phi] ~ sum w phi / sum w and
+       the effective sample size is sir_sum_w^2 / sir_sum_w2 (FP64 sums of
+       FP32 terms; their last bits depend on the launch shape). */
+    uint64_t n_kept;
+    double sir_sum_w, sir_sum_w2, sir_sum_wS; /* sum w, w^2, w S (S = H2/E0) */
+    double sir_sum_w_u0[4];                   /* sum w u0^p, p = 1..4 */
 } tkdv_stats;
 
 /* Accepted-sample record, as stored in the device ring and returned by
@@ -144,7 +162,8 @@ typedef struct {
 typedef struct {
     uint64_t idx;    /* proposal index within its point's stream */
     uint32_t point;  /* point number within the handle (0-based) */
-    uint32_t flags;  /* bit 0: decided on the FP64 path; bit 1: near threshold */
+    uint32_t flags;  /* bit 0: decided on the FP64 path; bit 1: near threshold;
+                        bits 8..31: copies (SIR runs; 0 in rejection runs) */
     float H2, H3;    /* Eqs. (20) and (42) of the accepted state */
     float u0;        /* u(xi = 0) */
     float delta;     /* log f/(M g) */

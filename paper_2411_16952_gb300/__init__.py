@@ -52,13 +52,13 @@ class TkdvError(RuntimeError):
 class tkdv_point(C.Structure):
     _fields_ = [("beta_p", C.c_double), ("E0", C.c_double), ("r", C.c_double),
                 ("proposal", C.c_int), ("point_id", C.c_uint32), ("override_logM", C.c_int),
-                ("logM", C.c_double), ("log_var_correction", C.POINTER(C.c_double))]
+                ("logM", C.c_double), ("log_var_correction", C.POINTER(C.c_double)), ("sir_c", C.c_double)]
 
 
 class tkdv_options(C.Structure):
     _fields_ = [("K", C.c_int), ("h3_mode", C.c_int), ("grid_N", C.c_int),
                 ("sample_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
-                ("use_graph", C.c_int), ("ctas_per_sm", C.c_int), ("threads_per_cta", C.c_int)]
+                ("use_graph", C.c_int), ("ctas_per_sm", C.c_int), ("threads_per_cta", C.c_int), ("sir", C.c_int)]
 
 
 class tkdv_stats(C.Structure):
@@ -69,7 +69,9 @@ class tkdv_stats(C.Structure):
                 ("alpha_star", C.c_double), ("sum_u0", C.c_double * 4), ("mean", C.c_double),
                 ("var", C.c_double), ("skew", C.c_double), ("kurt", C.c_double),
                 ("hist", C.c_uint64 * HIST_BINS), ("hist_lo", C.c_double), ("hist_hi", C.c_double),
-                ("exceed", C.c_uint64 * N_EXCEED), ("spectrum", C.c_double * KMAX)]
+                ("exceed", C.c_uint64 * N_EXCEED), ("spectrum", C.c_double * KMAX), ("n_kept", C.c_uint64),
+                ("sir_sum_w", C.c_double), ("sir_sum_w2", C.c_double), ("sir_sum_wS", C.c_double),
+                ("sir_sum_w_u0", C.c_double * 4)]
 
 
 _lock = threading.Lock()
@@ -424,7 +426,8 @@ def _stats_dict(s):
             "var": s.var, "skew": s.skew, "kurt": s.kurt,
             "hist": np.array(s.hist[:], dtype=np.uint64), "hist_lo": s.hist_lo,
             "hist_hi": s.hist_hi, "exceed": np.array(s.exceed[:], dtype=np.uint64),
-            "spectrum": np.array(s.spectrum[:])}
+            "spectrum": np.array(s.spectrum[:]), "n_kept": s.n_kept, "sir_sum_w": s.sir_sum_w,
+            "sir_sum_w2": s.sir_sum_w2, "sir_sum_wS": s.sir_sum_wS, "sir_sum_w_u0": np.array(s.sir_sum_w_u0[:])}
 
 
 def decode_records(buf, K):
@@ -434,6 +437,7 @@ def decode_records(buf, K):
     return {"idx": raw[:, 0:8].copy().view(np.uint64).reshape(n),
             "point": raw[:, 8:12].copy().view(np.uint32).reshape(n),
             "flags": raw[:, 12:16].copy().view(np.uint32).reshape(n),
+            "copies": (raw[:, 12:16].copy().view(np.uint32).reshape(n) >> 8).astype(np.int64),
             "H2": raw[:, 16:20].copy().view(np.float32).reshape(n),
             "H3": raw[:, 20:24].copy().view(np.float32).reshape(n),
             "u0": raw[:, 24:28].copy().view(np.float32).reshape(n),
@@ -441,9 +445,10 @@ def decode_records(buf, K):
             "xhat": raw[:, 32:32 + 8 * K].copy().view(np.float32).reshape(n, 2 * K)}
 
 
-def make_point(beta_p, E0, r, proposal=PROPOSAL_PAPER, point_id=0, logM=None, log_var_correction=None):
+def make_point(beta_p, E0, r, proposal=PROPOSAL_PAPER, point_id=0, logM=None, log_var_correction=None, sir_c=1.0):
     p = tkdv_point()
     p.beta_p, p.E0, p.r, p.proposal, p.point_id = beta_p, E0, r, proposal, point_id
+    p.sir_c = float(sir_c)
     if logM is not None:
         p.override_logM, p.logM = 1, float(logM)
     if log_var_correction is not None:
@@ -457,7 +462,7 @@ class Sampler:
     """One handle of the C library (several parameter points, one K)."""
 
     def __init__(self, K, points, h3_mode=H3_TRIAD_F32, grid_N=0, sample_capacity=1 << 20,
-                 stream=None, use_graph=True, ctas_per_sm=0, threads_per_cta=0):
+                 stream=None, use_graph=True, ctas_per_sm=0, threads_per_cta=0, sir=False):
         self.K = K
         self.n_points = len(points)
         o = tkdv_options()
@@ -471,6 +476,7 @@ class Sampler:
             o.cuda_stream = C.c_void_p(handle if handle != 0 else 1)
         o.use_graph = 1 if use_graph else 0
         o.ctas_per_sm, o.threads_per_cta = ctas_per_sm, threads_per_cta
+        o.sir = 1 if sir else 0
         self.h = sampler_create_ex(points, o)
 
     def run(self, n_proposals, seed):

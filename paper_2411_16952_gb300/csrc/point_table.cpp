@@ -87,6 +87,8 @@ void fill_point_const(int K, const tkdv_point &q, const double *s2, double logM,
         // sum_j U_j^2 = (N/2)|x|^2 the error of T is below 2^-14.4 sqrt(2K)
         c.guard_h += (float)(std::ldexp(1.0, -14) * std::sqrt(2.0 * K) * std::fabs(c.cH_d));
     }
+    c.sir_c = q.sir_c > 0 ? q.sir_c : 1.0;
+    c.sir_lnc = (float)std::log(c.sir_c);
     c.point_id = q.point_id;
     c.K = K;
 }

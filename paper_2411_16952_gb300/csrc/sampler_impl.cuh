@@ -108,8 +108,12 @@ __device__ __forceinline__ float rho_acc(uint32_t w) {
     const float ser = (2.f * t) * fmaf(t, fmaf(t, 1.f / 3.f, 0.5f), 1.f);
     return w >= 0xFF800000u ? ser : rho_fast(w);
 }
-// 1/sqrt(rho) above which a draw holds a radius of the series range (rho < 2^-8)
-constexpr float kSmallRhoRsqrt = 15.5f;
+// Outputs: an error e in rho moves the projected component of mode m by at
+// most sigma_m e / (2 sqrt(rho_m) |x|); with rho_fast's 3.3e-7 above the
+// series range and |x| >= 4 that stays below 1e-6 while sigma_m/sqrt(rho_m)
+// <= 24.  An accepted draw whose largest sigma_m/sqrt(rho_m) exceeds this
+// (about 1 % of them) takes its outputs from rho_acc instead.
+constexpr float kSmallRhoRsqrt = 24.f;
 
 // Box-Muller pair in FP32, scaled by s: rho = -2 ln u1 (the squared radius),
 // and (x, y) = s sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
@@ -144,7 +148,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // Scalar constants of the current point, held in registers.
 struct Scal {
-    float cS, cH, cQ, logM, u0s, h3s, E0, ga, gr, gh, ge, gq, ha, hb, ea;
+    float cS, cH, cQ, logM, u0s, h3s, E0, ga, gr, gh, ge, gq, ha, hb, ea, lnc;
     uint32_t pid;
     int K;
 };
@@ -163,6 +167,7 @@ __device__ __forceinline__ Scal load_scal(const PointConst *P) {
     s.gh = __ldg(&P->guard_h);
     s.ge = __ldg(&P->guard_e);
     s.gq = __ldg(&P->guard_q);
+    s.lnc = __ldg(&P->sir_lnc);
     s.ha = __ldg(&P->hist_a);
     s.hb = __ldg(&P->hist_b);
     s.ea = __ldg(&P->exc_a);
@@ -182,7 +187,7 @@ struct Draw {
     float u0raw;    // sum_k x_k                = u(0) |x| / u0s
     uint32_t wmin;  // smallest radius word: below kTailBucket the draw needs the FP64 pass
     float esum;     // sum_m sigma_m / sqrt(rho_m): scales the radius-error guard
-    float rrmax;    // largest 1/sqrt(rho_m): above kSmallRhoRsqrt outputs need rho_acc
+    float rrmax;    // largest sigma_m/sqrt(rho_m): above kSmallRhoRsqrt outputs need rho_acc
 };
 
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
@@ -208,8 +213,9 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
                 float rho, xm, ym, rr;
                 box_muller_f32<ACC>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
                 d.wmin = min(d.wmin, h ? w.z : w.x);
-                d.esum = fmaf(s, rr, d.esum);
-                d.rrmax = fmaxf(d.rrmax, s > 0.f ? rr : 0.f);
+                const float srr = s * rr;
+                d.esum += srr;
+                d.rrmax = fmaxf(d.rrmax, srr);
                 d.x[m] = xm;
                 d.y[m] = ym;
                 const float sk = (s * s) * rho;
@@ -329,7 +335,7 @@ __device__ __forceinline__ int exc_bin(float u0, float a) {
 
 // ---- FP64 evaluation of one proposal (guard band, replay) -----------------
 struct Out64 {
-    double delta, lnU, S, T;
+    double delta, lnU, u, S, T;
     float H2, H3, u0;
     int accept, near;
 };
@@ -383,7 +389,8 @@ __device__ __noinline__ void eval64(const PointConst *P, unsigned long long idx,
     delta -= P->logM;
     const uint32_t wa = accept_word(lo, hi, pid, K, k0, k1);
     o->delta = delta;
-    o->lnU = log(u01d_ext(wa, 4u * (uint32_t)((K + 1) / 2), lo, hi, pid, k0, k1));
+    o->u = u01d_ext(wa, 4u * (uint32_t)((K + 1) / 2), lo, hi, pid, k0, k1);
+    o->lnU = log(o->u);
     o->accept = o->lnU < delta;
     o->near = fabs(o->lnU - delta) < 1e-6;
     o->H2 = (float)((double)P->E0 * o->S);
@@ -474,13 +481,14 @@ __device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long lo
 }
 
 // ---- the persistent sampler ----------------------------------------------
-template <int KMAX, bool UNIF, int NT, int MINB>
+template <int KMAX, bool UNIF, int NT, int MINB, bool SIR = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_sample_triad(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1) {
     __shared__ uint32_t s_hist[kHistBins];
     __shared__ uint32_t s_exc[kExcBins];
     __shared__ unsigned long long s_q[4];
     __shared__ unsigned long long s_spec[KMAX];
+    __shared__ double s_sir[SIR ? 7 : 1];
     __shared__ uint32_t s_cnt[4];  // accepted, envelope violations, dropped, fallbacks
     __shared__ uint32_t s_maxd;
     __shared__ uint32_t s_chunk;
@@ -489,6 +497,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const int tid = threadIdx.x, lane = tid & 31;
     for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
     for (int e = tid; e < KMAX; e += NT) s_spec[e] = 0ull;
+    if (SIR && tid < 7) s_sir[tid] = 0.0;
     if (tid < kExcBins) s_exc[tid] = 0;
     if (tid < 4) {
         s_q[tid] = 0ull;
@@ -525,6 +534,7 @@ __global__ void __launch_bounds__(NT, MINB)
         __syncthreads();
 
         float maxd = -INFINITY;
+        float a_sir[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // SIR: w, w^2, w S, w u0^p
         for (uint32_t i0 = 0; i0 < n_here; i0 += NT) {
             const uint32_t i = i0 + (uint32_t)tid;
             const bool valid = i < n_here;
@@ -536,7 +546,31 @@ __global__ void __launch_bounds__(NT, MINB)
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
             // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
             const bool tail = min(dr.wmin, wa) < kTailBucket;
-            bool defer = valid && (fabsf(f.d) < f.guard || tail);
+            bool defer;
+            if (SIR) {
+                // at least one copy needs U < P(N >= 1) = 1 - exp(-lambda),
+                // lambda = c exp(delta); every proposal that may get one goes
+                // to the FP64 pass, which draws its copy number exactly
+                const float lnT1 = logf(-expm1f(-expf(f.delta + sc.lnc)));
+                defer = valid && (f.lnU - lnT1 < f.guard + sc.gr * fabsf(lnT1) + 1e-6f || tail);
+                if (valid) {
+                    const float w = expf(f.delta);
+                    const float u0 = sc.u0s * dr.u0raw * f.inv;
+                    a_sir[0] += w;
+                    a_sir[1] = fmaf(w, w, a_sir[1]);
+                    a_sir[2] = fmaf(w, f.S, a_sir[2]);
+                    float pw = w * u0;
+                    a_sir[3] += pw;
+                    pw *= u0;
+                    a_sir[4] += pw;
+                    pw *= u0;
+                    a_sir[5] += pw;
+                    pw *= u0;
+                    a_sir[6] += pw;
+                }
+            } else {
+                defer = valid && (fabsf(f.d) < f.guard || tail);
+            }
             if (valid && !tail) maxd = fmaxf(maxd, f.delta);
 
             // guard band -> FP64 queue
@@ -561,8 +595,8 @@ __global__ void __launch_bounds__(NT, MINB)
                     }
                 }
             }
-            const bool acc = valid && !defer && f.d < 0.f;
-            if (valid && !defer && f.delta > 0.f) atomicAdd(&s_cnt[1], 1u);
+            const bool acc = !SIR && valid && !defer && f.d < 0.f;
+            if (!SIR && valid && !defer && f.delta > 0.f) atomicAdd(&s_cnt[1], 1u);
 
             const unsigned ma = __ballot_sync(0xffffffffu, acc);
             if (ma) {
@@ -599,8 +633,21 @@ __global__ void __launch_bounds__(NT, MINB)
         uint32_t key = fkey(maxd);
         key = __reduce_max_sync(0xffffffffu, key);
         if (lane == 0 && maxd > -INFINITY) atomicMax(&s_maxd, key);
+        if (SIR) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                float v = a_sir[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) atomicAdd(&s_sir[q], (double)v);
+            }
+        }
         __syncthreads();
         StatBlock *st = B.stats + p;
+        if (SIR && tid < 7) {
+            atomicAdd(&st->sir[tid], s_sir[tid]);
+            s_sir[tid] = 0.0;
+        }
         for (int e = tid; e < kHistBins; e += NT) {
             if (s_hist[e]) {
                 atomicAdd(&st->hist[e], (unsigned long long)s_hist[e]);
@@ -635,6 +682,31 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 }
 
+// ---- SIR copy numbers in FP64 ---------------------------------------------
+// P(N >= k) for N ~ Poisson(lambda), k >= 1: for lambda <= k + 1 the series
+// lambda^k e^-lambda / k! * sum_i lambda^i k! / (k + i)! (all terms positive),
+// otherwise 1 - e^-lambda sum_{j<k} lambda^j / j!.
+static __device__ double poisson_tail_d(double lambda, int k) {
+    if (!(lambda > 0.0)) return 0.0;
+    if (lambda <= k + 1.0) {
+        const double lead = exp(k * log(lambda) - lambda - lgamma(k + 1.0));
+        double term = 1.0, sum = 1.0;
+        for (int i = 1; i < 256; ++i) {
+            term *= lambda / (double)(k + i);
+            sum += term;
+            if (term < 1e-18 * sum) break;
+        }
+        return lead * sum;
+    }
+    double p = exp(-lambda), s = p;
+    for (int j = 1; j < k; ++j) {
+        p *= lambda / (double)j;
+        s += p;
+    }
+    return 1.0 - s;
+}
+constexpr int kMaxCopies = (1 << 24) - 1;  // copies fit the record's 24-bit field
+
 // ---- FP64 decision of the guard-band proposals ---------------------------
 template <int KMAX, bool UNIF>
 __global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t k1) {
@@ -648,21 +720,41 @@ __global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t
         eval64<KMAX, UNIF>(P, it.idx, k0, k1, &o, xh);
         atomicAdd(&st->n_refined, 1ull);
         atomicMax(&st->maxd_key, (unsigned long long)fkey((float)o.delta));
-        if (o.near) atomicAdd(&st->n_near, 1ull);
-        if (o.delta > 0.0) atomicAdd(&st->n_viol, 1ull);
-        if (!o.accept) continue;
-        atomicAdd(&st->n_acc, 1ull);
+        unsigned long long copies = 1;
+        if (B.sir) {
+            // SIR: n = #{k >= 1 : U < P(N >= k)}, N ~ Poisson(c exp(delta))
+            const double lam = P->sir_c * exp(o.delta);
+            int n = 0;
+            double tk = poisson_tail_d(lam, 1);
+            while (n < kMaxCopies && o.u < tk) {
+                ++n;
+                tk = poisson_tail_d(lam, n + 1);
+            }
+            // near: U within 1e-6 (in log) of the tail value that decided n
+            const double tn = n > 0 ? poisson_tail_d(lam, n) : 1.0;
+            const bool near = fabs(o.lnU - log(tk)) < 1e-6 || (n > 0 && fabs(o.lnU - log(tn)) < 1e-6);
+            o.near = near;
+            if (near) atomicAdd(&st->n_near, 1ull);
+            if (n == 0) continue;
+            atomicAdd(&st->n_kept, 1ull);
+            copies = (unsigned long long)n;
+        } else {
+            if (o.near) atomicAdd(&st->n_near, 1ull);
+            if (o.delta > 0.0) atomicAdd(&st->n_viol, 1ull);
+            if (!o.accept) continue;
+        }
+        atomicAdd(&st->n_acc, copies);
         const float u0 = o.u0;
-        atomicAdd(&st->hist[hist_bin(u0, __ldg(&P->hist_a), __ldg(&P->hist_b))], 1ull);
-        atomicAdd(&st->exc[exc_bin(u0, __ldg(&P->exc_a))], 1ull);
+        atomicAdd(&st->hist[hist_bin(u0, __ldg(&P->hist_a), __ldg(&P->hist_b))], copies);
+        atomicAdd(&st->exc[exc_bin(u0, __ldg(&P->exc_a))], copies);
         const float u2 = u0 * u0;
-        atomicAdd(&st->q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
-        atomicAdd(&st->q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
-        atomicAdd(&st->q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
-        atomicAdd(&st->q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+        atomicAdd(&st->q[0], copies * (unsigned long long)__float2ll_rn(u0 * kQ1));
+        atomicAdd(&st->q[1], copies * (unsigned long long)__float2ll_rn(u2 * kQ2));
+        atomicAdd(&st->q[2], copies * (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+        atomicAdd(&st->q[3], copies * (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
         for (int m = 0; m < P->K; ++m)
-            atomicAdd(&st->spec[m],
-                      (unsigned long long)__float2ull_rn(fmaf(xh[m], xh[m], xh[P->K + m] * xh[P->K + m]) * kSpecScale));
+            atomicAdd(&st->spec[m], copies * (unsigned long long)__float2ull_rn(
+                                                 fmaf(xh[m], xh[m], xh[P->K + m] * xh[P->K + m]) * kSpecScale));
         const unsigned long long slot = atomicAdd(B.ring_count, 1ull);
         if (slot < B.ring_cap) {
             const int K = P->K;
@@ -670,7 +762,7 @@ __global__ void __launch_bounds__(128) k_refine(DevBufs B, uint32_t k0, uint32_t
             *reinterpret_cast<unsigned long long *>(rec) = it.idx;
             uint32_t *h = reinterpret_cast<uint32_t *>(rec + 8);
             h[0] = it.point;
-            h[1] = 1u | (o.near ? 2u : 0u);
+            h[1] = 1u | (o.near ? 2u : 0u) | (B.sir ? (uint32_t)copies << 8 : 0u);
             float *f = reinterpret_cast<float *>(rec + 16);
             f[0] = o.H2;
             f[1] = o.H3;
@@ -750,6 +842,8 @@ void fill_triad_kernels(TriadKernels *t) {
     t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128, 1>;
     t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256, 1>;
     t->main[1][2] = (const void *)k_sample_triad<KMAX, true, 256, 2>;
+    t->sir[0] = (const void *)k_sample_triad<KMAX, false, 256, 1, true>;
+    t->sir[1] = (const void *)k_sample_triad<KMAX, true, 256, 1, true>;
     t->refine[0] = (const void *)k_refine<KMAX, false>;
     t->refine[1] = (const void *)k_refine<KMAX, true>;
     t->replay[0] = (const void *)k_replay<KMAX, false>;

@@ -153,6 +153,7 @@ bool is_grid(const tkdv_sampler *h) { return h->opt.h3_mode == TKDV_H3_GRID_BF16
 const void *main_fn(const tkdv_sampler *h, int variant) {
     const int uni = h->all_uniform ? 1 : 0;
     if (is_grid(h)) return h->kg.main[uni];
+    if (h->opt.sir) return h->kt.sir[uni];  // one form (256 threads)
     return h->kt.main[uni][variant];
 }
 
@@ -391,6 +392,13 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     }
     if (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "threads_per_cta must be 0, 128 or 256");
+    if (opt->sir != 0 && opt->sir != 1) return fail(nullptr, TKDV_ERR_INVALID_ARG, "sir must be 0 or 1");
+    if (opt->sir && opt->h3_mode != TKDV_H3_TRIAD_F32)
+        return fail(nullptr, TKDV_ERR_UNSUPPORTED, "SIR runs use the triad form");
+    if (opt->sir)
+        for (int p = 0; p < n_points; ++p)
+            if (!(points[p].sir_c > 0) || !std::isfinite(points[p].sir_c))
+                return fail(nullptr, TKDV_ERR_INVALID_ARG, "SIR: every point needs sir_c > 0");
     tkdv_sampler *h = new tkdv_sampler();
     h->K = opt->K;
     h->kmax = kmax_for(opt->K);
@@ -434,6 +442,10 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     }
     h->launch.threads = opt->threads_per_cta ? opt->threads_per_cta : 256;
     h->launch.variant = h->launch.threads == 128 ? 0 : 1;
+    if (opt->sir) {
+        h->launch.threads = 256;
+        h->launch.variant = 1;
+    }
     if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
         int major = 0;
         e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
@@ -516,6 +528,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     h->dev.ring_cap = cap;
     h->dev.rec_bytes = (uint32_t)h->rec_bytes;
     h->dev.refine_cap = kRefineCap;
+    h->dev.sir = opt->sir;
     if ((rc = set_default_launch(h))) return bail(rc);
     *out = h;
     return TKDV_OK;
@@ -617,6 +630,11 @@ int sampler_stats(tkdv_sampler *h, tkdv_stats *out, int n_out) {
             o.exceed[i] = t;
         }
         for (int m = 0; m < h->K && m < TKDV_KMAX; ++m) o.spectrum[m] = (double)s.spec[m] / (double)kSpecScale;
+        o.n_kept = s.n_kept;
+        o.sir_sum_w = s.sir[0];
+        o.sir_sum_w2 = s.sir[1];
+        o.sir_sum_wS = s.sir[2];
+        for (int q = 0; q < 4; ++q) o.sir_sum_w_u0[q] = s.sir[3 + q];
     }
     return rc;
 }
@@ -726,6 +744,7 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
     float best_ms = 1e30f;
     std::vector<int> var_list = {0, 1, 2};
     if (is_grid(h)) var_list = {0};
+    if (h->opt.sir) var_list = {1};
     (void)uni;
     for (int var : var_list) {
         const int thr = is_grid(h) ? 128 : kTriadVariantThreads[var];

@@ -51,6 +51,9 @@ struct PointConst {
     uint32_t point_id;
     int K;
     float guard_e, guard_q;  // per-draw guard terms for the radius error (point_table.cpp)
+    double sir_c;            // SIR: copies per unit exp(log f/(Mg))
+    float sir_lnc;           // ln sir_c
+    float pad2;
 };
 
 // Statistics of one point on the device: only integers, so that the result
@@ -64,6 +67,8 @@ struct StatBlock {
     unsigned long long n_fallback;  // guard-band proposals decided in FP32 (queue full)
     unsigned long long pad[2];
     unsigned long long spec[kKMax];  // sum of round(s_k * kSpecScale), s_k = xh_k^2 + xh_{K+k}^2
+    unsigned long long n_kept;       // SIR: proposals with at least one copy
+    double sir[7];                   // SIR: sum w, w^2, w S, w u0^p (p = 1..4), w = exp(delta), FP32 terms
 };
 
 struct RefineItem {
@@ -84,6 +89,7 @@ struct DevBufs {
     unsigned long long ring_cap;
     uint32_t rec_bytes;
     uint32_t refine_cap;
+    int sir;  // 1: the FP64 pass draws SIR copy numbers instead of accept bits
 };
 
 constexpr uint32_t kStatusRefineOverflow = 1u;
@@ -108,6 +114,7 @@ struct TriadKernels {
     // [uniform][variant]: 0: 128 threads; 1: 256 threads; 2: 256 threads held
     // to 128 registers (two CTAs per SM)
     const void *main[2][3];
+    const void *sir[2];  // SIR form of the sampler (256 threads), [uniform]
     const void *refine[2];
     const void *replay[2];
 };
