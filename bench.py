@@ -270,13 +270,17 @@ def main():
     clk = Clocks(local)  # started before any warm-up so that its start-up stays out of the timed steps
     forms = {"triad_f32_paper": (T.H3_TRIAD_F32, T.PROPOSAL_PAPER),
              "grid_bf16x3_paper": (T.H3_GRID_BF16X3, T.PROPOSAL_PAPER),
-             "grid_bf16x3_learned": (T.H3_GRID_BF16X3, T.PROPOSAL_LEARNED)}
+             "grid_bf16x3_learned": (T.H3_GRID_BF16X3, T.PROPOSAL_LEARNED),
+             # SIR with c = 1: the expected copies per proposal equal the
+             # rejection acceptance (lambda = exp(log f/(Mg)))
+             "sir_triad_paper": (T.H3_TRIAD_F32, T.PROPOSAL_PAPER)}
     if args.forms:
         unknown = set(args.forms.split(",")) - set(forms)
         if unknown:
             raise SystemExit("unknown form(s) %s; known: %s" % (sorted(unknown), sorted(forms)))
         forms = {k: v for k, v in forms.items() if k in args.forms.split(",")}
-    headline = next((f for f in ("grid_bf16x3_learned", "grid_bf16x3_paper") if f in forms), next(iter(forms)))
+    headline = next((f for f in ("grid_bf16x3_learned", "grid_bf16x3_paper", "triad_f32_paper") if f in forms),
+                    next(iter(forms)))
     learned_info = None
     if "grid_bf16x3_learned" in forms:
         # the learned proposal is trained (outside the timed region) on accepted
@@ -301,7 +305,7 @@ def main():
         else:
             points = [T.make_point(bp, E0, r, prop, point_id=pid) for bp, r, pid in pts]
         S = T.Sampler(K, points, h3_mode=mode, grid_N=gN if mode == T.H3_GRID_BF16X3 else 0,
-                      sample_capacity=1 << 21, stream=stream)
+                      sample_capacity=1 << 21, stream=stream, sir=fname.startswith("sir"))
         if not args.no_autotune:
             S.autotune(1 << 22)
         seed = 0
@@ -368,7 +372,7 @@ def main():
         bw = workloads.batch_k32()
         bpts = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]), T.PROPOSAL_PAPER,
                              point_id=rank * 64 + p) for p in range(64)]
-        best_form = max((f for f in results if f != "grid_bf16x3_learned"),
+        best_form = max((f for f in results if f in ("triad_f32_paper", "grid_bf16x3_paper")),
                         key=lambda f: results[f]["proposals_per_s"])
         bmode = T.H3_GRID_BF16X3 if best_form.startswith("grid") else T.H3_TRIAD_F32
         SB = T.Sampler(bw["K"], bpts, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,

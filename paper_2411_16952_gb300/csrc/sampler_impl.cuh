@@ -110,10 +110,10 @@ __device__ __forceinline__ float rho_acc(uint32_t w) {
 }
 // Outputs: an error e in rho moves the projected component of mode m by at
 // most sigma_m e / (2 sqrt(rho_m) |x|); with rho_fast's 3.3e-7 above the
-// series range and |x| >= 4 that stays below 1e-6 while sigma_m/sqrt(rho_m)
-// <= 24.  An accepted draw whose largest sigma_m/sqrt(rho_m) exceeds this
-// (about 1 % of them) takes its outputs from rho_acc instead.
-constexpr float kSmallRhoRsqrt = 24.f;
+// series range that stays below 1e-6 while max_m sigma_m / sqrt(rho_m) / |x|
+// <= 6.  An accepted draw above it (about 1 % of them at K = 32) takes its
+// outputs from rho_acc instead.
+constexpr float kOutputRr = 6.f;
 
 // Box-Muller pair in FP32, scaled by s: rho = -2 ln u1 (the squared radius),
 // and (x, y) = s sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
@@ -187,7 +187,7 @@ struct Draw {
     float u0raw;    // sum_k x_k                = u(0) |x| / u0s
     uint32_t wmin;  // smallest radius word: below kTailBucket the draw needs the FP64 pass
     float esum;     // sum_m sigma_m / sqrt(rho_m): scales the radius-error guard
-    float rrmax;    // largest sigma_m/sqrt(rho_m): above kSmallRhoRsqrt outputs need rho_acc
+    float rrmax;    // largest sigma_m/sqrt(rho_m): above kOutputRr |x| outputs need rho_acc
 };
 
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(NT, MINB)
                         rec = B.ring + slot * B.rec_bytes;
                     else
                         atomicAdd(&s_cnt[2], 1u);
-                    if (dr.rrmax > kSmallRhoRsqrt) {
+                    if (dr.rrmax * f.inv > kOutputRr) {
                         // a radius of the series range: outputs from rho_acc
                         emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
                                                   s_spec, rec);
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
     }
     row[2] = f.d < 0.f ? 1.0 : 0.0;
     row[3] = 0.0;
-    if (dr.rrmax > kSmallRhoRsqrt) {
+    if (dr.rrmax * f.inv > kOutputRr) {
         // a radius of the series range: the values are those of rho_acc, as
         // the sampler's outputs of an accepted draw would be
         draw_fast<KMAX, UNIF, true>(dr, P->sigma, P->act, lo, hi, sc.pid, k0, k1);
