@@ -184,9 +184,9 @@ int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv
 /* sampler_create_ex: n_points (1..64) points sharing opt->K and opt->h3_mode,
    run together by one persistent launch (batched form).  Errors as above,
    plus UNSUPPORTED for the grid form on a device without tcgen05.  The grid
-   form runs K <= 16 and K <= 32 with two 128-proposal tiles per CTA and
-   K <= 64 with one (shared memory: 2 x grid_N x 128 x 2 B basis plus 64 KB
-   per tile, 2x for K > 32). */
+   form runs K <= 16 with two 128-proposal tiles per CTA and K <= 32 and
+   K <= 64 with one (shared memory: 2 x grid_N x 2K x 2 B basis plus
+   2 x 128 x 2K x 2 B per tile). */
 int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options *opt,
                       tkdv_sampler **out);
 
