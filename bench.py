@@ -67,7 +67,7 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (321024.0 / (8 * 4194304), "ncu --set full capture prof_grid22 (k_sample_grid<32,0,2>)"),
+    "grid": (158720.0 / (8 * 4194304), "ncu --set full capture prof_grid24 (k_sample_grid<32,0,1>)"),
     "triad": (139008.0 / (8 * 4194304), "ncu --set full capture prof_triad22 (k_sample_triad<32,0,256,1,0>)"),
 }
 
@@ -372,34 +372,39 @@ def main():
         bw = workloads.batch_k32()
         bpts = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]), T.PROPOSAL_PAPER,
                              point_id=rank * 64 + p) for p in range(64)]
-        best_form = max((f for f in results if f in ("triad_f32_paper", "grid_bf16x3_paper")),
-                        key=lambda f: results[f]["proposals_per_s"])
-        bmode = T.H3_GRID_BF16X3 if best_form.startswith("grid") else T.H3_TRIAD_F32
-        SB = T.Sampler(bw["K"], bpts, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,
-                       sample_capacity=1 << 22, stream=stream)
-        if not args.no_autotune:
-            SB.autotune(1 << 20)
-        for _ in range(args.warmup):
-            SB.run_budgets(bw["budgets"], 7)
-        SB.sync()
-        SB.reset()
-        bev = []
-        for _ in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            SB.run_budgets(bw["budgets"], 7)
-            e1.record(stream)
-            bev.append((e0, e1))
-        torch.cuda.synchronize()
-        bms = sum(a.elapsed_time(b_) for a, b_ in bev) / args.steps
-        bst = SB.stats()
-        bprop = sum(s["n_proposals"] for s in bst)
-        bacc = sum(s["n_accepted"] for s in bst)
-        batch = {"workload": bw["name"], "form": best_form, "proposals_per_step": bprop // args.steps,
-                 "ms_per_step": bms, "proposals_per_s": bprop / (bms * args.steps / 1e3),
-                 "accepted_per_s": bacc / (bms * args.steps / 1e3), "launch": SB.launch_config()}
-        SB.close()
+        # both forms: the batch's acceptances reach 0.5, where the grid form's
+        # per-accept redraw weighs more than on the headline workload
+        bforms = {}
+        for best_form in [f for f in ("triad_f32_paper", "grid_bf16x3_paper") if f in results]:
+            bmode = T.H3_GRID_BF16X3 if best_form.startswith("grid") else T.H3_TRIAD_F32
+            SB = T.Sampler(bw["K"], bpts, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,
+                           sample_capacity=1 << 22, stream=stream)
+            if not args.no_autotune:
+                SB.autotune(1 << 20)
+            for _ in range(args.warmup):
+                SB.run_budgets(bw["budgets"], 7)
+            SB.sync()
+            SB.reset()
+            bev = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                SB.run_budgets(bw["budgets"], 7)
+                e1.record(stream)
+                bev.append((e0, e1))
+            torch.cuda.synchronize()
+            bms = sum(a.elapsed_time(b_) for a, b_ in bev) / args.steps
+            bst = SB.stats()
+            bprop = sum(s["n_proposals"] for s in bst)
+            bacc = sum(s["n_accepted"] for s in bst)
+            bforms[best_form] = {"proposals_per_step": bprop // args.steps, "ms_per_step": bms,
+                                 "proposals_per_s": bprop / (bms * args.steps / 1e3),
+                                 "accepted_per_s": bacc / (bms * args.steps / 1e3), "launch": SB.launch_config()}
+            SB.close()
+        if bforms:
+            best_form = max(bforms, key=lambda f: bforms[f]["proposals_per_s"])
+            batch = dict(bforms[best_form], workload=bw["name"], form=best_form, forms=bforms)
 
     h = results[headline]
     form_kind = "grid" if headline.startswith("grid") else "triad"
@@ -438,7 +443,7 @@ def main():
                    "parallelism": "points x index ranges, weak per GPU"},
         "roofline": roof,
         "e2e": h.get("e2e"),
-        "gpu_launches": 2 * args.steps * len(forms) + (2 * args.steps if batch else 0),
+        "gpu_launches": 2 * args.steps * len(forms) + (2 * args.steps * len(batch["forms"]) if batch else 0),
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
