@@ -119,7 +119,11 @@ typedef struct {
                                  the same proposal (named in Sec. IV.B): every proposal carries the weight
                                  exp(log f/(Mg)) and is kept n ~ Poisson(sir_c exp(log f/(Mg))) times, n drawn
                                  by inversion of its accept uniform, n = #{k >= 1 : U < P(N >= k)}; given
-                                 their total the copies are the multinomial SIR draw.  Triad form only. */
+                                 their total the copies are the multinomial SIR draw.  Triad form only.
+                                 Every proposal that may get a copy is decided in the FP64 pass, which
+                                 holds 4M proposals per run: keep sir_c sum exp(log f/(Mg)) per run well
+                                 below that; proposals beyond it get no copy and are counted in
+                                 n_fallback. */
 } tkdv_options;
 
 /* Statistics of one point, accumulated over runs until sampler_reset().
