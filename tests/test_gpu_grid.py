@@ -2,7 +2,7 @@
 N > 3K points) with the FP64 oracle and with the FP32 triad form.
 
 Tolerances: per sample, H = H2 - (C3/C2) H3 within 1e-5 (|H2| + |C3/C2 H3|)
-of the oracle (the BF16 x3 split keeps it near 2e-6, see DESIGN.md); accept
+of the oracle (the BF16 x3 split keeps it near 2e-6); accept
 decisions identical to the oracle's except draws within 1e-6 of the threshold,
 and identical to the triad form's (both decide the guard band in FP64).
 """

@@ -151,7 +151,7 @@ def test_trained_network_gain(T):
     each point: the predicted acceptance gain exp(log M_paper - log M_learned)
     (exact, because the corrections have mean zero), the measured acceptance
     ratio over 2^24 proposals per proposal kind, and the ensemble statistics of
-    the two proposals (the paper's Sigma judges the learned one).  In this
+    the two proposals (the paper's Sigma is the yardstick for the learned one).  In this
     family of proposals the gain is small (the paper's Sigma is near the best
     per-mode variance profile); the test pins prediction = measurement and
     that the learned proposal samples the same Gibbs measure."""
