@@ -26,7 +26,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KMAX = 64
+KMAX = 128
 HIST_BINS = 256
 N_EXCEED = 25
 UNIFORM, PAPER, DIAG = 0, 1, 2

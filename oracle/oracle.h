@@ -20,7 +20,7 @@
 extern "C" {
 #endif
 
-#define ORC_KMAX 64
+#define ORC_KMAX 128
 #define ORC_HIST_BINS 256
 #define ORC_EXCEED 25
 
@@ -30,7 +30,7 @@ extern "C" {
 #define ORC_PROPOSAL_DIAG 2    /* any diagonal Gaussian with pair variances sigma2[k] */
 
 typedef struct {
-    int K;          /* Galerkin cutoff, 1..64 (Eq. 8) */
+    int K;          /* Galerkin cutoff, 1..128 (Eq. 8) */
     int proposal;   /* ORC_PROPOSAL_* */
     double E0;      /* energy, Eq. (5) */
     double beta_p;  /* normalised inverse temperature beta', Eq. (21) */

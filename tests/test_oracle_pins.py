@@ -139,7 +139,7 @@ def test_appendix_A_two_mode_exact():
             assert abs(O.H3_double(2, E0, xh) - 2 * math.pi * R2 * R1**2 * math.cos(2 * t1 - t2)) < 1e-14
 
 
-@pytest.mark.parametrize("K", [1, 2, 3, 8, 16, 32, 64])
+@pytest.mark.parametrize("K", [1, 2, 3, 8, 16, 32, 64, 128])
 def test_H3_three_forms_agree(K):
     """Double sum (Eq. 42) = triple sum (Eq. 41) = grid cubature of Eq. (2) with N > 3K."""
     rng = np.random.default_rng(K)
@@ -161,13 +161,13 @@ def test_grid_needs_more_than_3K_points():
 
 def test_H3_structure():
     rng = np.random.default_rng(4)
-    for K in (4, 16, 32):
+    for K in (4, 16, 32, 128):
         for k in range(1, K + 1):  # a single active mode forms no triad
             xh = np.zeros(2 * K)
             ph = rng.uniform(0, 2 * math.pi)
             xh[k - 1], xh[K + k - 1] = math.cos(ph), math.sin(ph)
             assert abs(O.H3_double(K, 1.0, xh)) < 1e-15
-            assert abs(O.H2(K, 1.0, xh) - k * k) < 1e-12
+            assert abs(O.H2(K, 1.0, xh) - k * k) < 1e-13 * k * k
         xh = rand_sphere(rng, K)
         assert abs(O.H3_double(K, 1.0, -xh) + O.H3_double(K, 1.0, xh)) < 1e-15  # odd
         assert O.H2(K, 1.0, -xh) == O.H2(K, 1.0, xh)  # even
@@ -196,10 +196,45 @@ def test_energy_constraint_after_projection():
             assert abs(0.5 * np.sum(u * u) * 2 * math.pi / N - 1.7) < 1e-12
 
 
+def test_K128_replay_records():
+    """K = 128, the largest cutoff: every replayed record lies on the sphere,
+    its H3 equals the grid cubature of Eq. (2) with 3K + 1 points (a formula
+    independent of the double sum), H2 = E0 S with S = sum k^2 s_k, and u0 is
+    the field at xi = 0.  The normals of the upper modes (Philox blocks 32-63)
+    are standard and uncorrelated with those of the lower modes, and the
+    accept uniform (block 64) is uniform."""
+    K, E0, seed, pid = 128, 1.0, 7, 3
+    pt = O.make_point(K, E0, 60.0, 150.0, O.PAPER, logM=0.0)
+    rec = O.replay(pt, seed, pid, np.arange(48, dtype=np.uint64), nthreads=2)
+    k = np.arange(1, K + 1)
+    for i in range(48):
+        xh = rec["xhat"][i][:2 * K]
+        assert abs(np.sum(xh * xh) - 1.0) < 1e-13
+        S = float(np.dot(k * k, xh[:K] ** 2 + xh[K:] ** 2))
+        assert abs(rec["S"][i] - S) < 1e-9 * S
+        assert abs(rec["H2"][i] - E0 * S) < 1e-9 * S
+        assert abs(rec["H3"][i] - O.H3_grid(K, E0, xh, 3 * K + 1)) < 1e-12
+        assert abs(rec["u0"][i] - O.u_at(K, E0, xh, 0.0)) < 1e-12
+    n = 3000
+    zs, us = [], []
+    for i in range(n):
+        z, u = O.stream(K, seed, pid, i)
+        zs.append(z)
+        us.append(u)
+    zs, us = np.array(zs), np.array(us)
+    hi = np.concatenate([zs[:, 64:K], zs[:, K + 64:]], axis=1)
+    lo = np.concatenate([zs[:, :64], zs[:, K:K + 64]], axis=1)
+    assert abs(hi.mean()) < 0.01 and abs(hi.var() - 1.0) < 0.015
+    c = np.mean(hi * lo, axis=0)  # pairwise products of mode m and mode m - 64
+    assert np.max(np.abs(c)) < 5.0 / math.sqrt(n)
+    assert abs(us.mean() - 0.5) < 0.02 and abs(us.var() - 1.0 / 12) < 0.01
+    assert abs(np.corrcoef(us, zs[:, K - 1])[0, 1]) < 0.08
+
+
 def test_dirichlet_kernel():
     """Eq. (46): u_k = sqrt(E0/(2 pi K)); its peak u(0) is the largest displacement
     any field of energy E0 reaches (Cauchy-Schwarz), and H3 = pi K (K-1) c^3."""
-    for K in (16, 32):
+    for K in (16, 32, 128):
         xh = np.zeros(2 * K)
         xh[:K] = 1 / math.sqrt(K)
         cp = math.sqrt(1.0 / (2 * math.pi * K))
