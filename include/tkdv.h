@@ -14,7 +14,7 @@
  *   Eq. (16).
  *
  * Conventions used throughout
- *   - K in [1, 64] complex modes; a state is the real vector
+ *   - K in [1, 128] complex modes; a state is the real vector
  *     xhat = [xhat_1..xhat_K | xhat_{K+1}..xhat_{2K}] (cosine half | sine
  *     half), u_k = sqrt(E0/2pi) (xhat_k - i xhat_{K+k}) (Eq. 16).
  *   - r is the ratio C3/C2 of Eq. (43).  Together with K, E0 and beta' it is
@@ -83,7 +83,7 @@ int tkdv_check_radius_error(double *max_ratio, uint32_t *worst_word);
 #define TKDV_MAX_POINTS 64
 #define TKDV_HIST_BINS 256
 #define TKDV_N_EXCEED 25
-#define TKDV_KMAX 64
+#define TKDV_KMAX 128
 
 /* One parameter point (Sec. IV.A: K, E0, beta', C3/C2 are the only parameters). */
 typedef struct {
@@ -106,7 +106,9 @@ typedef struct {
 
 /* Options shared by all points of one handle. */
 typedef struct {
-    int K;                    /* modes, 1..64, common to all points of the handle */
+    int K;                    /* modes, 1..128, common to all points of the handle; the triad form runs
+                                 K <= 64 one proposal per thread and 65..128 one warp per four proposals
+                                 (same stream, same decisions); the grid form and SIR need K <= 64 */
     int h3_mode;              /* TKDV_H3_* */
     int grid_N;               /* grid points for TKDV_H3_GRID_BF16X3: multiple of 32, > 3K, <= 256;
                                  0: the smallest such (128 for K = 32) */
@@ -181,7 +183,7 @@ typedef struct tkdv_sampler tkdv_sampler;
    triad H3, 2^20-record ring, own stream).  Runs the per-point precompute of
    Sec. IV.B on the host: alpha* (Eq. 29), sigma_k (Eq. 25) and log M
    (Eq. 45), then allocates device buffers.  The 4th argument is C3/C2.
-   Errors: INVALID_ARG (K outside 1..64, E0 <= 0, beta' < 0, unknown
+   Errors: INVALID_ARG (K outside 1..128, E0 <= 0, beta' < 0, unknown
    proposal), NO_ALPHA, OOM, CUDA.  *out is NULL on error. */
 int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv_sampler **out);
 
@@ -290,7 +292,7 @@ int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint
    stream capture.  Every call shares the array: each call clears it first,
    and calls whose work overlaps on the GPU (other host threads, other
    streams) race on it and must not be issued.
-     K           modes, 1..64
+     K           modes, 1..128
      point       host struct; override_logM must be 1 with the envelope in
                  logM (tkdv_log_M computes it), else TKDV_ERR_INVALID_ARG
      n_proposals at most TKDV_STATIC_MAX_PROPOSALS, else TKDV_ERR_TOO_LARGE

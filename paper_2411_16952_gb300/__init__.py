@@ -30,7 +30,7 @@ H3_TRIAD_F32, H3_GRID_BF16X3 = 0, 1
 MAX_POINTS = 64
 HIST_BINS = 256
 N_EXCEED = 25
-KMAX = 64
+KMAX = 128
 
 EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler_run",
             "sampler_run_budgets", "sampler_run_ranges", "sampler_stats", "sampler_samples",

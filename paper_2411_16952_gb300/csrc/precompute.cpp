@@ -246,7 +246,7 @@ extern "C" int tkdv_alpha_star(int K, double beta_p, double *out) {
 }
 
 extern "C" int tkdv_log_M(int K, double beta_p, double E0, double r, const double *sigma2, double *out) {
-    if (K < 1 || K > 64 || !(E0 > 0) || !(beta_p >= 0) || !std::isfinite(r) || !out)
+    if (K < 1 || K > TKDV_KMAX || !(E0 > 0) || !(beta_p >= 0) || !std::isfinite(r) || !out)
         return TKDV_ERR_INVALID_ARG;
     Objective ob;
     ob.K = K;

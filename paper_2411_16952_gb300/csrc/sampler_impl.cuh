@@ -848,6 +848,7 @@ void fill_triad_kernels(TriadKernels *t) {
     t->refine[1] = (const void *)k_refine<KMAX, true>;
     t->replay[0] = (const void *)k_replay<KMAX, false>;
     t->replay[1] = (const void *)k_replay<KMAX, true>;
+    t->replay_per_block = 128;
 }
 
 }  // namespace tkdv

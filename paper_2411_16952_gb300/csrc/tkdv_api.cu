@@ -84,7 +84,7 @@ int fail(tkdv_sampler *h, int code, const std::string &msg) {
 }
 
 int kmax_for(int K) {
-    for (int m : {4, 8, 16, 32, 64})
+    for (int m : {4, 8, 16, 32, 64, 128})
         if (K <= m) return m;
     return 0;
 }
@@ -380,7 +380,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (!points || !opt) return fail(nullptr, TKDV_ERR_INVALID_ARG, "points/options NULL");
     if (n_points < 1 || n_points > kMaxPoints)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "n_points must be in 1..64");
-    if (opt->K < 1 || opt->K > kKMax) return fail(nullptr, TKDV_ERR_INVALID_ARG, "K must be in 1..64");
+    if (opt->K < 1 || opt->K > kKMax) return fail(nullptr, TKDV_ERR_INVALID_ARG, "K must be in 1..128");
     if (opt->h3_mode != TKDV_H3_TRIAD_F32 && opt->h3_mode != TKDV_H3_GRID_BF16X3)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "unknown h3_mode");
     int gridN = 0;
@@ -395,6 +395,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (opt->sir != 0 && opt->sir != 1) return fail(nullptr, TKDV_ERR_INVALID_ARG, "sir must be 0 or 1");
     if (opt->sir && opt->h3_mode != TKDV_H3_TRIAD_F32)
         return fail(nullptr, TKDV_ERR_UNSUPPORTED, "SIR runs use the triad form");
+    if (opt->sir && opt->K > 64) return fail(nullptr, TKDV_ERR_UNSUPPORTED, "SIR runs need K <= 64");
     if (opt->sir)
         for (int p = 0; p < n_points; ++p)
             if (!(points[p].sir_c > 0) || !std::isfinite(points[p].sir_c))
@@ -426,7 +427,8 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
         case 8: triad_kernels_k8(&h->kt); break;
         case 16: triad_kernels_k16(&h->kt); break;
         case 32: triad_kernels_k32(&h->kt); break;
-        default: triad_kernels_k64(&h->kt); break;
+        case 64: triad_kernels_k64(&h->kt); break;
+        default: triad_kernels_k128(&h->kt); break;
     }
     auto bail = [&](int rc) {
         g_create_error = h->err;
@@ -722,7 +724,8 @@ int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint
     void *args[] = {(void *)&P, &d_idx, &nn, &k0, &k1, &d_out};
     e = cudaMemcpyAsync(d_idx, idx, 8 * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaLaunchKernel(h->kt.replay[uni], dim3((unsigned)((n + 127) / 128)), dim3(128), args, 0, h->stream);
+        e = cudaLaunchKernel(h->kt.replay[uni], dim3((unsigned)((n + h->kt.replay_per_block - 1) / h->kt.replay_per_block)),
+                             dim3(128), args, 0, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double) * row * n, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(d_idx);

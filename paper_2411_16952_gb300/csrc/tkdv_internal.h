@@ -11,7 +11,7 @@
 
 namespace tkdv {
 
-constexpr int kKMax = 64;
+constexpr int kKMax = 128;
 constexpr int kMaxPoints = 64;
 constexpr int kHistBins = 256;
 constexpr int kExcBins = 26;  // exceed-bin e = number of thresholds 0.25 i sigma0 below u0
@@ -117,12 +117,15 @@ struct TriadKernels {
     const void *sir[2];  // SIR form of the sampler (256 threads), [uniform]
     const void *refine[2];
     const void *replay[2];
+    int replay_per_block;  // indices one replay CTA of 128 threads handles
 };
 void triad_kernels_k4(TriadKernels *t);
 void triad_kernels_k8(TriadKernels *t);
 void triad_kernels_k16(TriadKernels *t);
 void triad_kernels_k32(TriadKernels *t);
 void triad_kernels_k64(TriadKernels *t);
+// 65..128 modes: one warp per batch of four proposals (sampler_k128.cu).
+void triad_kernels_k128(TriadKernels *t);
 
 // Kernel table of one KMAX instantiation of the grid (tensor-core) sampler.
 struct GridKernels {

@@ -99,8 +99,8 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     TriadKernels kt{};
-    int kmax = 64;
-    for (int m : {4, 8, 16, 32, 64})
+    int kmax = 128;
+    for (int m : {4, 8, 16, 32, 64, 128})
         if (K <= m) {
             kmax = m;
             break;
@@ -110,7 +110,8 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
         case 8: triad_kernels_k8(&kt); break;
         case 16: triad_kernels_k16(&kt); break;
         case 32: triad_kernels_k32(&kt); break;
-        default: triad_kernels_k64(&kt); break;
+        case 64: triad_kernels_k64(&kt); break;
+        default: triad_kernels_k128(&kt); break;
     }
     const int uni = point->proposal == TKDV_PROPOSAL_UNIFORM ? 1 : 0;
     const void *fn = kt.main[uni][1];

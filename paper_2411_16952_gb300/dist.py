@@ -11,6 +11,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import KMAX
+
 INT_KEYS = ("n_proposals", "n_accepted", "n_near_threshold", "n_refined", "n_envelope_violations",
             "n_dropped", "n_fallback")
 
@@ -38,7 +40,7 @@ def merge_stats(stats, group=None):
     P = len(stats)
     ints = np.array([[s[k] for k in INT_KEYS] + list(s["hist"]) + list(s["exceed"]) for s in stats],
                     dtype=np.int64)
-    sums = np.array([list(s["sum_u0"]) + list(s.get("spectrum", np.zeros(64))) for s in stats],
+    sums = np.array([list(s["sum_u0"]) + list(s.get("spectrum", np.zeros(KMAX))) for s in stats],
                     dtype=np.float64)
     mx = np.array([s["max_delta"] for s in stats], dtype=np.float64)
     ti, ts, tm = torch.from_numpy(ints), torch.from_numpy(sums), torch.from_numpy(mx)

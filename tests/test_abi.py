@@ -71,7 +71,7 @@ def test_create_without_gpu_fails_loudly(libtkdv):
 
 def test_invalid_arguments_are_rejected(libtkdv):
     import paper_2411_16952_gb300 as T
-    for args, code in [((0, 20.0, 1.0, 0.0, 1), -1), ((65, 20.0, 1.0, 0.0, 1), -1),
+    for args, code in [((0, 20.0, 1.0, 0.0, 1), -1), ((129, 20.0, 1.0, 0.0, 1), -1),
                        ((16, -1.0, 1.0, 0.0, 1), -1), ((16, 20.0, 0.0, 0.0, 1), -1),
                        ((16, 20.0, 1.0, 0.0, 7), -1), ((16, 1e4, 1.0, 0.0, 1), -2)]:
         with pytest.raises(T.TkdvError) as ei:
@@ -80,7 +80,7 @@ def test_invalid_arguments_are_rejected(libtkdv):
 
 
 @pytest.mark.parametrize("K,bp", [(1, 0.5), (2, 3.0), (8, 30.0), (16, 20.0), (32, 20.0), (32, 60.0),
-                                  (64, 40.0), (16, 0.0)])
+                                  (64, 40.0), (16, 0.0), (128, 20.0), (128, 60.0)])
 def test_library_alpha_star_matches_oracle(libtkdv, K, bp):
     import paper_2411_16952_gb300 as T
     assert abs(T.tkdv_alpha_star(K, bp) - O.alpha_star(K, bp)) < 1e-13
@@ -99,3 +99,16 @@ def test_library_envelope_matches_oracle(libtkdv, K, E0, bp, r, prop):
     s2 = np.array(pt.sigma2[:K]) if prop == O.PAPER else None
     lm_l = T.tkdv_log_M(K, bp, E0, r, s2)
     assert abs(lm_l - lm_o) < 1e-8 * (1 + abs(lm_o)), (lm_l, lm_o)
+
+
+@pytest.mark.parametrize("bp", [20.0, 60.0])
+def test_library_envelope_K128_closed_form(libtkdv, bp):
+    """K = 128, C3/C2 = 0: log f/g depends on the state only through S, so its
+    maximum has a closed form (pinned in the oracle tests); the library's
+    L-BFGS search over the 256-dimensional sphere reaches it."""
+    import paper_2411_16952_gb300 as T
+    from test_oracle_pins import logM_r0_paper
+    K = 128
+    pt = O.make_point(K, 1.0, bp, 0.0, O.PAPER)
+    lm_l = T.tkdv_log_M(K, bp, 1.0, 0.0, np.array(pt.sigma2[:K]))
+    assert abs(lm_l - logM_r0_paper(K, bp)) < 1e-9 * (1 + abs(lm_l))

@@ -124,7 +124,7 @@ def test_small_k16_full_replay(T, prop):
 # ------------------------------------------------------------ per-stage replay
 REPLAY_CASES = [(1, 0.6, 0.5, 10.0), (2, 1.3, 3.0, 40.0), (3, 1.0, 5.0, 30.0), (5, 0.8, 10.0, 60.0),
                 (8, 1.0, 30.0, 50.0), (16, 1.0, 20.0, 75.0), (17, 2.0, 25.0, 40.0), (32, 1.0, 40.0, 225.0),
-                (64, 1.0, 40.0, 400.0)]
+                (64, 1.0, 40.0, 400.0), (100, 1.0, 40.0, 225.0), (128, 1.0, 60.0, 150.0)]
 
 
 @pytest.mark.parametrize("K,E0,bp,r", REPLAY_CASES)
