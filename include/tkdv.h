@@ -59,17 +59,23 @@ extern "C" {
 #define TKDV_ERR_TIMEOUT (-5)     /* a device wait hit its iteration limit; results of that run are void */
 #define TKDV_ERR_UNSUPPORTED (-6) /* requested form not available on this device */
 #define TKDV_ERR_ENVELOPE (-7)    /* envelope search failed (non-finite log M) */
-#define TKDV_ERR_TOO_LARGE (-8)   /* tkdv_check_radius_error: diagnostic (the paper has no counterpart).  The
-   FP32 fast path computes the Box-Muller radius rho = -2 ln u of the uniform
-   map's 2^23 values with the hardware base-2 logarithm; its accept guard band
-   assumes |rho_f32 - rho| <= 2^-21 + 2^-21 rho.  This runs all 2^23 values on
-   the current device against an FP64 logarithm and returns the largest ratio
-   of the error to that bound (at most 1 if the assumption holds) and a word
-   that attains it (worst_word may be NULL).  Allocates 8 bytes of device
-   memory for the call.  Errors: INVALID_ARG (max_ratio NULL), OOM, CUDA. */
+#define TKDV_ERR_TOO_LARGE (-8)   /* sampler_run_static: more proposals than its fixed scratch holds */
+
+/* tkdv_check_radius_error: diagnostic (the paper has no counterpart).  The
+   one-thread fast path (K <= 64) computes the Box-Muller radius rho = -2 ln u
+   of the uniform map's 2^23 values with the hardware base-2 logarithm; its
+   accept guard band assumes |rho_f32 - rho| <= 2^-21 + 2^-21 rho.  This runs
+   all 2^23 values on the current device against an FP64 logarithm and returns
+   the largest ratio of the error to that bound (at most 1 if the assumption
+   holds) and a word that attains it (worst_word may be NULL).  Allocates 8
+   bytes of device memory for the call.  Errors: INVALID_ARG (max_ratio NULL),
+   OOM, CUDA. */
 int tkdv_check_radius_error(double *max_ratio, uint32_t *worst_word);
 
-/* sampler_run_static: more proposals than its fixed scratch holds */
+/* tkdv_check_radius_error_log: the same check for the warp form (K > 64),
+   whose radius is -2 logf(u) with the full-precision logarithm; its guard band
+   assumes the purely relative bound |rho_f32 - rho| <= 2^-22 rho. */
+int tkdv_check_radius_error_log(double *max_ratio, uint32_t *worst_word);
 
 /* ---- proposal kinds (Sec. III) ------------------------------------------ */
 #define TKDV_PROPOSAL_UNIFORM 0 /* uniform measure mu0 on the sphere (Eq. 15); the naive baseline */

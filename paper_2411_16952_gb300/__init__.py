@@ -37,7 +37,8 @@ EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler
             "sampler_reset", "sampler_sync", "sampler_set_deadline_ns", "sampler_point_info",
             "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
             "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static",
-            "sampler_set_trace", "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
+            "sampler_set_trace", "tkdv_check_radius_error", "tkdv_check_radius_error_log",
+            "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
             "tkdv_mlp_features", "tkdv_mlp_get_params", "tkdv_mlp_set_params", "tkdv_mlp_infer",
             "tkdv_mlp_set_data", "tkdv_mlp_set_data_records", "tkdv_mlp_rows", "tkdv_mlp_step"]
 MLP_NPARAM = 8640
@@ -127,6 +128,7 @@ def lib():
             L.tkdv_alpha_star.argtypes = [i, d, dp]
             L.tkdv_log_M.argtypes = [i, d, d, d, dp, dp]
             L.tkdv_check_radius_error.argtypes = [dp, C.POINTER(C.c_uint32)]
+            L.tkdv_check_radius_error_log.argtypes = [dp, C.POINTER(C.c_uint32)]
             L.sampler_field_maxima.argtypes = [vp, u64, dp, C.POINTER(C.c_int32), u64p]
             L.sampler_run_static.argtypes = [i, C.POINTER(tkdv_point), u64, u64, u64, vp, u64, u64p,
                                              C.POINTER(tkdv_stats), vp]
@@ -161,6 +163,14 @@ def tkdv_check_radius_error():
     uniform map (runs on the device)."""
     err, w = C.c_double(), C.c_uint32()
     _check(lib().tkdv_check_radius_error(C.byref(err), C.byref(w)))
+    return err.value, w.value
+
+
+def tkdv_check_radius_error_log():
+    """The same for the warp form's radius -2 logf(u) (K > 64) against its
+    purely relative bound 2^-22 rho."""
+    err, w = C.c_double(), C.c_uint32()
+    _check(lib().tkdv_check_radius_error_log(C.byref(err), C.byref(w)))
     return err.value, w.value
 
 

@@ -72,16 +72,30 @@ void fill_point_const(int K, const tkdv_point &q, const double *s2, double logM,
     // derivative below 3n per mode on the sphere, and |T| <= sqrt(K)), ln Q by
     // 2E/sqrt(n) through n and by K eps (1 + max sigma^2) / n through the raw
     // normals.
-    const double gam = 8.0 * (2.0 * K + 16.0) * std::ldexp(1.0, -24) + 4.0 * kRhoRelErr;
+    //
+    // The warp form (K > 64, sampler_k128.cu) sums differently: a mode sum
+    // (|x|^2, S|x|^2, Q|x|^2) passes each term through at most 12 roundings
+    // (its own 3, 4 per lane, 5 in the warp tree), a triad term through at most
+    // 50 (8 on its anti-diagonal, 31 in its tile, 3 over rounds, 5 in the warp
+    // tree, 3 in the scaling), so chains of 32 and 64 replace 2K + 16; the
+    // hardware sine and cosine add at most 2^-21.4 = 6.1 ulp per component,
+    // well inside the factor eight.  Its radius -2 logf(u) has no absolute
+    // error and a relative one below kRhoLogRelErr, so the per-draw terms (3)
+    // vanish.
+    const bool warp = K > 64;
+    const double eps = std::ldexp(1.0, -24);
+    const double rel = warp ? kRhoLogRelErr : kRhoRelErr, abs_err = warp ? 0.0 : kRhoAbsErr;
+    const double gam = 8.0 * (warp ? 32.0 : 2.0 * K + 16.0) * eps + 4.0 * rel;
+    const double gam_t = 8.0 * (warp ? 64.0 : 2.0 * K + 16.0) * eps + 4.0 * rel;
     c.guard_abs = (float)(1e-6 + gam * std::fabs(c.cQ_d));
     c.guard_rel = (float)gam;
-    c.guard_h = (float)(gam * std::fabs(c.cH_d) * std::sqrt((double)K));
+    c.guard_h = (float)(gam_t * std::fabs(c.cH_d) * std::sqrt((double)K));
     double smax = 0.0;
     for (int k = 0; k < K; ++k) smax = std::max(smax, s2[k]);
-    c.guard_e = (float)(2.0 * kRhoAbsErr *
+    c.guard_e = (float)(2.0 * abs_err *
                         (4.0 * K2 * std::fabs(c.cS_d) + 6.0 * std::sqrt((double)K) * std::fabs(c.cH_d) +
                          2.0 * std::fabs(c.cQ_d)));
-    c.guard_q = (float)(std::fabs(c.cQ_d) * K * kRhoAbsErr * (1.0 + smax));
+    c.guard_q = (float)(std::fabs(c.cQ_d) * K * abs_err * (1.0 + smax));
     if (grid) {
         // BF16 hi/lo x3: |dU_j| <= 2^-15.4 sqrt(2K) |x| per grid value, so with
         // sum_j U_j^2 = (N/2)|x|^2 the error of T is below 2^-14.4 sqrt(2K)

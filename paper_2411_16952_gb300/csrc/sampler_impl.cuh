@@ -115,6 +115,13 @@ __device__ __forceinline__ float rho_acc(uint32_t w) {
 // outputs from rho_acc instead.
 constexpr float kOutputRr = 6.f;
 
+// rho_log: the radius of the warp form (65..128 modes), the full-precision
+// logarithm (at most 1 ulp): |rho_log - rho| <= kRhoLogRelErr rho, no absolute
+// part (tkdv_check_radius_error_log measures it over all 2^23 values).  Its
+// outputs need no second pass, and its decision guard has no per-draw radius
+// terms.
+__device__ __forceinline__ float rho_log(uint32_t w) { return -2.f * logf(u01f(w)); }
+
 // Box-Muller pair in FP32, scaled by s: rho = -2 ln u1 (the squared radius),
 // and (x, y) = s sqrt(rho) (cos 2 pi u2, sin 2 pi u2).  The angle is reduced
 // exactly to 2 pi (u2 - 1/2) in (-pi, pi), where the hardware sine/cosine have

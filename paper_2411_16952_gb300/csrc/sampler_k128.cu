@@ -115,7 +115,7 @@ __device__ __forceinline__ float sel4(const float *a, int q) {
 // One batch of the fast path: the four proposals' draws, reductions and T.
 // On return every lane holds the values of proposal ql = lane & 3.
 struct WEval {
-    float nrm2, Sraw, zz, u0raw, esum, T;
+    float nrm2, Sraw, zz, u0raw, T;
     uint32_t wmin;
 };
 
@@ -123,16 +123,16 @@ template <bool UNIF>
 __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, const float *sig, const float *act,
                                             int K, const uint32_t *lo, const uint32_t *hi, uint32_t vmask,
                                             uint32_t pid, uint32_t k0, uint32_t k1, int lane) {
-    float nrm2[kWQ], Sraw[kWQ], zz[kWQ], u0raw[kWQ], esum[kWQ];
+    float nrm2[kWQ], Sraw[kWQ], zz[kWQ], u0raw[kWQ];
     uint32_t wmin[kWQ];
 #pragma unroll
     for (int q = 0; q < kWQ; ++q) {
-        nrm2[q] = Sraw[q] = zz[q] = u0raw[q] = esum[q] = 0.f;
+        nrm2[q] = Sraw[q] = zz[q] = u0raw[q] = 0.f;
         wmin[q] = 0xFFFFFFFFu;
     }
     // Steps 1-3: lane L makes the Philox blocks L and L + 32 of every proposal.
-    // Outputs of accepted draws need no second pass: the radius is rho_acc,
-    // whose error bound is that of rho_fast, so it serves the decision too.
+    // The radius is rho_log (purely relative error), so the outputs of
+    // accepted draws need no second pass and the guard no per-draw terms.
 #pragma unroll
     for (int i = 0; i < 2 * kWQ; ++i) {
         const int q = i >> 1;
@@ -143,10 +143,12 @@ __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, cons
             for (int h = 0; h < 2; ++h) {
                 const int m = 2 * j + h;
                 const float s = UNIF ? act[m] : sig[m];
-                float rho, xm, ym, rr;
-                box_muller_f32<true>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                const float rho = rho_log(h ? w.z : w.x);
+                const float a = (-s * rho) * rsqrtf(rho);
+                float sn, cs;
+                __sincosf(angle_f(h ? w.w : w.y), &sn, &cs);
+                const float xm = a * cs, ym = a * sn;
                 if (m < K) wmin[q] = min(wmin[q], h ? w.z : w.x);
-                esum[q] += s * rr;
                 sv[q * kWS + wpos(m)] = make_float2(xm, ym);
                 const float sk = (s * s) * rho;
                 nrm2[q] += sk;
@@ -162,7 +164,6 @@ __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, cons
         Sraw[q] = wsum(Sraw[q]);
         zz[q] = wsum(zz[q]);
         u0raw[q] = wsum(u0raw[q]);
-        esum[q] = wsum(esum[q]);
         wmin[q] = __reduce_min_sync(0xffffffffu, wmin[q]);
     }
     __syncwarp();
@@ -184,7 +185,6 @@ __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, cons
     ev.Sraw = sel4(Sraw, ql);
     ev.zz = sel4(zz, ql);
     ev.u0raw = sel4(u0raw, ql);
-    ev.esum = sel4(esum, ql);
     ev.T = sel4(Tq, ql);
     ev.wmin = ql == 0 ? wmin[0] : ql == 1 ? wmin[1] : ql == 2 ? wmin[2] : wmin[3];
     return ev;
@@ -204,8 +204,8 @@ __device__ __forceinline__ Fast warp_eval(const WEval &ev, const Scal &c, uint32
     f.delta = ((tS + tH) + tQ) - c.logM;
     f.lnU = -0.5f * rho_fast(wacc);
     f.d = f.lnU - f.delta;
-    f.guard = fmaf(c.ge * ev.esum, f.inv,
-                   fmaf(c.gq, inv2, c.ga + c.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(f.lnU) + fabsf(c.logM)) + c.gh));
+    // the warp form's guard has no per-draw radius terms (guard_e = guard_q = 0)
+    f.guard = c.ga + c.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(f.lnU) + fabsf(c.logM)) + c.gh;
     return f;
 }
 
@@ -223,6 +223,183 @@ __device__ void wshared_init(WShared<NW> &sh, int tid, int nt) {
     for (int t = tid; t < 32 * kWRounds; t += nt) sh.tab[t] = tile_entry(t);
     float2 *v = &sh.v[0][0];
     for (int e = tid; e < NW * kWQ * kWS; e += nt) v[e] = make_float2(0.f, 0.f);
+}
+
+// ---- FP64 pass of the warp form -------------------------------------------
+// The same draw and formulas as eval64 (sampler_impl.cuh), spread over a warp:
+// lane L makes the modes of Philox blocks L and L + 32 into the slab sx (FP64
+// pairs, zero from K on), and the double sum of Eq. (42), folded,
+//   T = sum_{n=2}^{K} Re(conj(v_n) W_n),
+//   W_n = 2 sum_{k < n-k} v_k v_{n-k} + [n even] v_{n/2}^2,
+// takes rows n and 131 - n as one loop of 64 pairs (n = 3..65): two such
+// loops per lane, and row 2 on lane 31.  Rows above K read v_n = 0.  Every
+// lane returns the proposal's values.
+__device__ __forceinline__ double wsum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void row_end(const double2 *sx, int n, double A, double B, double &t) {
+    A *= 2.0;
+    B *= 2.0;
+    if ((n & 1) == 0) {
+        const double2 h = sx[n / 2 - 1];
+        A = fma(h.x, h.x, A);
+        A = fma(-h.y, h.y, A);
+        B = fma(2.0 * h.x, h.y, B);
+    }
+    const double2 vn = sx[n - 1];
+    t = fma(vn.x, A, t);
+    t = fma(vn.y, B, t);
+}
+
+// rows n1 < n2 with (n1 - 1)/2 + (n2 - 1)/2 = 64 folded pairs
+__device__ __forceinline__ void fold_pair(const double2 *sx, int n1, int n2, double &t) {
+    const int len1 = (n1 - 1) / 2;
+    double A = 0.0, B = 0.0;
+    int n = n1, k = 1;
+    for (int i = 0; i < 64; ++i) {
+        if (i == len1) {
+            row_end(sx, n1, A, B, t);
+            A = 0.0;
+            B = 0.0;
+            n = n2;
+            k = 1;
+        }
+        const double2 a = sx[k - 1], b = sx[n - k - 1];
+        A = fma(a.x, b.x, A);
+        A = fma(-a.y, b.y, A);
+        B = fma(a.x, b.y, B);
+        B = fma(a.y, b.x, B);
+        ++k;
+    }
+    row_end(sx, n2, A, B, t);
+}
+
+template <bool UNIF>
+__device__ __noinline__ void eval64_warp(const PointConst *P, unsigned long long idx, uint32_t k0, uint32_t k1,
+                                         double2 *sx, int lane, Out64 &o, double &inv_out) {
+    const int K = P->K;
+    const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32), pid = P->point_id;
+    double nrm2 = 0.0, Sraw = 0.0, zz = 0.0, u0raw = 0.0;
+    __syncwarp();  // earlier readers of the slab are done
+    for (int jj = 0; jj < 2; ++jj) {
+        const int j = lane + 32 * jj;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (2 * j < K) w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, pid), k0, k1);
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * j + h;
+            double2 v = make_double2(0.0, 0.0);
+            if (m < K) {
+                const double u1 = u01d_ext(h ? w.z : w.x, 2u * (uint32_t)m, lo, hi, pid, k0, k1);
+                const double u2 = u01d(h ? w.w : w.y);
+                const double rho = -2.0 * log(u1);
+                const double rad = sqrt(rho);
+                double sn, cs;
+                sincospi(2.0 * u2, &sn, &cs);
+                const double sg = UNIF ? 1.0 : P->sigma_d[m];
+                v.x = sg * rad * cs;
+                v.y = sg * rad * sn;
+                const double sk = v.x * v.x + v.y * v.y;
+                nrm2 += sk;
+                Sraw += (double)((m + 1) * (m + 1)) * sk;
+                zz += rho;
+                u0raw += v.x;
+            }
+            sx[m] = v;
+        }
+    }
+    __syncwarp();
+    double t = 0.0;
+    fold_pair(sx, 3 + lane, 128 - lane, t);
+    if (lane < 31)
+        fold_pair(sx, 35 + lane, 96 - lane, t);
+    else
+        row_end(sx, 2, 0.0, 0.0, t);
+    const double T = wsum_d(t);
+    nrm2 = wsum_d(nrm2);
+    Sraw = wsum_d(Sraw);
+    zz = wsum_d(zz);
+    u0raw = wsum_d(u0raw);
+    const double inv = 1.0 / sqrt(nrm2);
+    const double inv2 = inv * inv;
+    o.S = Sraw * inv2;
+    o.T = T * inv2 * inv;
+    double delta = P->cS_d * o.S + P->cH_d * o.T;
+    if (!UNIF) delta += P->cQ_d * log(zz * inv2);
+    delta -= P->logM;
+    const uint32_t wa = accept_word(lo, hi, pid, K, k0, k1);
+    o.delta = delta;
+    o.u = u01d_ext(wa, 4u * (uint32_t)((K + 1) / 2), lo, hi, pid, k0, k1);
+    o.lnU = log(o.u);
+    o.accept = o.lnU < delta;
+    o.near = fabs(o.lnU - delta) < 1e-6;
+    o.H2 = (float)((double)P->E0 * o.S);
+    o.H3 = (float)((double)P->h3s * o.T);
+    o.u0 = (float)((double)P->u0s * u0raw * inv);
+    inv_out = inv;
+}
+
+// FP64 decision of the guard-band proposals, one warp per queued proposal.
+template <bool UNIF>
+__global__ void __launch_bounds__(128) k_refine_warp(DevBufs B, uint32_t k0, uint32_t k1) {
+    __shared__ double2 s_x[4][kWK];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double2 *sx = s_x[warp];
+    const uint32_t n = min(*(volatile uint32_t *)&B.counters[1], B.refine_cap);
+    for (uint32_t i = blockIdx.x * 4u + (uint32_t)warp; i < n; i += gridDim.x * 4u) {
+        const RefineItem it = B.refine[i];
+        const PointConst *P = B.pts + it.point;
+        StatBlock *st = B.stats + it.point;
+        Out64 o;
+        double inv;
+        eval64_warp<UNIF>(P, it.idx, k0, k1, sx, lane, o, inv);
+        if (lane == 0) {
+            atomicAdd(&st->n_refined, 1ull);
+            atomicMax(&st->maxd_key, (unsigned long long)fkey((float)o.delta));
+            if (o.near) atomicAdd(&st->n_near, 1ull);
+            if (o.delta > 0.0) atomicAdd(&st->n_viol, 1ull);
+        }
+        if (!o.accept) continue;  // the same in every lane
+        const int K = P->K;
+        unsigned long long slot = 0;
+        if (lane == 0) {
+            atomicAdd(&st->n_acc, 1ull);
+            const float u0 = o.u0, u2 = u0 * u0;
+            atomicAdd(&st->hist[hist_bin(u0, __ldg(&P->hist_a), __ldg(&P->hist_b))], 1ull);
+            atomicAdd(&st->exc[exc_bin(u0, __ldg(&P->exc_a))], 1ull);
+            atomicAdd(&st->q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
+            atomicAdd(&st->q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
+            atomicAdd(&st->q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+            atomicAdd(&st->q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+            slot = atomicAdd(B.ring_count, 1ull);
+            if (slot >= B.ring_cap) atomicAdd(&st->n_dropped, 1ull);
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        unsigned char *rec = slot < B.ring_cap ? B.ring + slot * B.rec_bytes : nullptr;
+        float *xh = rec ? reinterpret_cast<float *>(rec + 32) : nullptr;
+        for (int m = lane; m < K; m += 32) {
+            const double2 v = sx[m];
+            const float xf = (float)(v.x * inv), yf = (float)(v.y * inv);
+            atomicAdd(&st->spec[m], (unsigned long long)__float2ull_rn(fmaf(xf, xf, yf * yf) * kSpecScale));
+            if (xh) {
+                xh[m] = xf;
+                xh[K + m] = yf;
+            }
+        }
+        if (rec && lane == 0) {
+            *reinterpret_cast<unsigned long long *>(rec) = it.idx;
+            uint32_t *h = reinterpret_cast<uint32_t *>(rec + 8);
+            h[0] = it.point;
+            h[1] = 1u | (o.near ? 2u : 0u);
+            float *f = reinterpret_cast<float *>(rec + 16);
+            f[0] = o.H2;
+            f[1] = o.H3;
+            f[2] = o.u0;
+            f[3] = (float)o.delta;
+        }
+    }
 }
 
 template <bool UNIF, int NT, int MINB>
@@ -418,6 +595,7 @@ __global__ void __launch_bounds__(32 * kReplayWarps) k_replay_warp(const PointCo
                                                                    unsigned long long n, uint32_t k0, uint32_t k1,
                                                                    double *out) {
     __shared__ WShared<kReplayWarps> sh;
+    __shared__ double2 s_x[kReplayWarps][kWK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ql = lane & 3;
     wshared_init<kReplayWarps>(sh, tid, 32 * kReplayWarps);
     for (int e = tid; e < kWK; e += 32 * kReplayWarps) {
@@ -447,22 +625,9 @@ __global__ void __launch_bounds__(32 * kReplayWarps) k_replay_warp(const PointCo
     const bool valid = lane < kWQ && ((vmask >> lane) & 1u);
     const bool slow = fabsf(f.d) < f.guard || min(ev.wmin, wa) < kTailBucket;
     const size_t rowlen = 8 + 2 * (size_t)K;
-    if (valid) {
+    if (valid && !slow) {
         double *row = out + (b0 + lane) * rowlen;
-        if (slow) {
-            Out64 o;
-            float xh[2 * kWK];
-            eval64<kWK, UNIF>(P, ((unsigned long long)hq << 32) | lq, k0, k1, &o, xh);
-            row[0] = o.delta;
-            row[1] = o.lnU;
-            row[2] = o.accept;
-            row[3] = 1.0 + (o.near ? 2.0 : 0.0);
-            row[4] = o.H2;
-            row[5] = o.H3;
-            row[6] = o.u0;
-            row[7] = o.S;
-            for (int m = 0; m < 2 * K; ++m) row[8 + m] = xh[m];
-        } else {
+        {
             row[0] = f.delta;
             row[1] = f.lnU;
             row[2] = f.d < 0.f ? 1.0 : 0.0;
@@ -471,6 +636,33 @@ __global__ void __launch_bounds__(32 * kReplayWarps) k_replay_warp(const PointCo
             row[5] = sc.h3s * f.T;
             row[6] = sc.u0s * ev.u0raw * f.inv;
             row[7] = f.S;
+        }
+    }
+    // the proposals of the FP64 pass, one after the other on the whole warp
+    unsigned ms = __ballot_sync(0xffffffffu, valid && slow);
+    while (ms) {
+        const int q = __ffs(ms) - 1;
+        ms &= ms - 1;
+        const unsigned long long id =
+            ((unsigned long long)__shfl_sync(0xffffffffu, hq, q) << 32) | __shfl_sync(0xffffffffu, lq, q);
+        Out64 o;
+        double inv;
+        eval64_warp<UNIF>(P, id, k0, k1, s_x[warp], lane, o, inv);
+        double *row = out + (b0 + q) * rowlen;
+        if (lane == 0) {
+            row[0] = o.delta;
+            row[1] = o.lnU;
+            row[2] = o.accept;
+            row[3] = 1.0 + (o.near ? 2.0 : 0.0);
+            row[4] = o.H2;
+            row[5] = o.H3;
+            row[6] = o.u0;
+            row[7] = o.S;
+        }
+        for (int m = lane; m < K; m += 32) {
+            const double2 v = s_x[warp][m];
+            row[8 + m] = (float)(v.x * inv);
+            row[8 + K + m] = (float)(v.y * inv);
         }
     }
     // projected state of the proposals decided in FP32, written by the warp
@@ -497,8 +689,8 @@ void triad_kernels_k128(TriadKernels *t) {
     t->main[1][1] = (const void *)k_sample_warp<true, 256, 1>;
     t->main[1][2] = (const void *)k_sample_warp<true, 256, 2>;
     t->sir[0] = t->sir[1] = nullptr;  // SIR runs use the one-thread form (K <= 64)
-    t->refine[0] = (const void *)k_refine<kWK, false>;
-    t->refine[1] = (const void *)k_refine<kWK, true>;
+    t->refine[0] = (const void *)k_refine_warp<false>;
+    t->refine[1] = (const void *)k_refine_warp<true>;
     t->replay[0] = (const void *)k_replay_warp<false>;
     t->replay[1] = (const void *)k_replay_warp<true>;
     t->replay_per_block = 32 * kReplayWarps / 32 * kWQ;

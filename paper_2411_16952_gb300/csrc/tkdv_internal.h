@@ -28,6 +28,9 @@ constexpr float kSpecScale = 268435456.0f;  // 2^28
 // |rho_fast - rho| <= kRhoAbsErr + kRhoRelErr * rho for every value of the map.
 constexpr double kRhoAbsErr = 0x1p-21;
 constexpr double kRhoRelErr = 0x1p-21;
+// The radius of the warp form (65..128 modes), -2 logf(u), has only a relative
+// error: |rho_log - rho| <= kRhoLogRelErr * rho for every value of the map.
+constexpr double kRhoLogRelErr = 0x1p-22;
 
 // Per-point constants, built on the host from the precompute (alpha*, sigma_k,
 // log M) and read by every proposal of that point.

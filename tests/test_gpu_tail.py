@@ -140,3 +140,12 @@ def test_fast_path_radius_error_bound(T):
     ratio, w = T.tkdv_check_radius_error()
     assert ratio <= 1.0, (ratio, w)
     print("radius: largest error / bound = %.3f at word %#x" % (ratio, w))
+
+
+def test_warp_form_radius_error_bound(T):
+    """The warp form's FP32 radius -2 logf(u) stays within the purely relative
+    bound 2^-22 rho its guard band is built on, over all 2^23 values of the
+    uniform map."""
+    ratio, w = T.tkdv_check_radius_error_log()
+    assert ratio <= 1.0, (ratio, w)
+    print("log radius: largest error / bound = %.3f at word %#x" % (ratio, w))
