@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--learn-accept", type=int, default=1 << 14, help="accepted samples per point to train on")
     ap.add_argument("--learn-steps", type=int, default=200)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-k128", action="store_true", help="skip the K = 128 measurement")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.impl == "reference":
@@ -406,6 +407,46 @@ def main():
             best_form = max(bforms, key=lambda f: bforms[f]["proposals_per_s"])
             batch = dict(bforms[best_form], workload=bw["name"], form=best_form, forms=bforms)
 
+    # K = 128 (one warp per four proposals, the cutoff of Fig. 7): eight points
+    k128 = None
+    if not args.no_k128:
+        from paper_2411_16952_gb300 import workloads
+        kw = workloads.speedup_k128()
+        kpts = [T.make_point(b, kw["E0"], r, T.PROPOSAL_PAPER, point_id=rank * 8 + p)
+                for p, (b, r) in enumerate(kw["points"])]
+        SK = T.Sampler(kw["K"], kpts, sample_capacity=1 << 20, stream=stream)
+        if not args.no_autotune:
+            SK.autotune(1 << 22)
+        for _ in range(args.warmup):
+            SK.run(kw["n"], 3)
+        SK.sync()
+        SK.reset()
+        kev = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            SK.run(kw["n"], 3)
+            e1.record(stream)
+            kev.append((e0, e1))
+        torch.cuda.synchronize()
+        kms = sum(a.elapsed_time(b_) for a, b_ in kev) / args.steps
+        kst = SK.stats()
+        kprop = sum(s["n_proposals"] for s in kst)
+        kacc = sum(s["n_accepted"] for s in kst)
+        kops = alg_ops_per_proposal(kw["K"], "triad")
+        kpeak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        kpps = kprop / (kms * args.steps / 1e3)
+        k128 = {"workload": kw["name"], "K": kw["K"], "ms_per_step": kms, "proposals_per_s": kpps,
+                "accepted_per_s": kacc / (kms * args.steps / 1e3), "acceptance": kacc / kprop,
+                "refined_fraction": sum(s["n_refined"] for s in kst) / kprop,
+                "envelope_violations": sum(s["n_envelope_violations"] for s in kst),
+                "launch": SK.launch_config(),
+                "alu": {"ops_per_proposal": kops, "achieved": kops * kpps / 1e12, "peak": kpeak,
+                        "unit": "Tops/s", "frac": kops * kpps / 1e12 / kpeak,
+                        "kernel": "k_sample_warp", "note": "same op count and peak as the headline roofline"}}
+        SK.close()
+
     h = results[headline]
     form_kind = "grid" if headline.startswith("grid") else "triad"
     ops = alg_ops_per_proposal(K, form_kind, gN)
@@ -436,7 +477,7 @@ def main():
         "headline_form": headline, "forms": results,
         "vs_plain_fp32": h["accepted_per_s"] / results["triad_f32_paper"]["accepted_per_s"]
         if "triad_f32_paper" in results else None,
-        "learned": learned_info, "batch_64pts": batch,
+        "learned": learned_info, "batch_64pts": batch, "k128": k128,
         "config": {"workload": wl["name"], "K": K, "grid_N": gN, "points": len(pts),
                    "proposals_per_point_per_step": n, "proposal": "paper",
                    "l2": "256 MiB buffer written between timed steps, outside the step events",

@@ -46,3 +46,13 @@ def batch_k32(seed=20241126):
     r = np.array([r_from_depth(b, d) for b, d in zip(bp, D)])
     budgets = (2 ** g.integers(18, 27, 64)).astype(np.uint64)
     return dict(name="K32_batch_64pts", K=32, beta_p=bp, E0=E0, D=D, r=r, budgets=budgets)
+
+
+def speedup_k128(n=1 << 24):
+    """K = 128 (the cutoff of the parallel-speedup test, Fig. 7), E0 = 1, the
+    beta' and C3/C2 of the extreme workload (eight beta' log-spaced over
+    [20, 60], beta' C3/C2 = 9000); the figure states no beta' or C3/C2.  2^24
+    proposals per point and step."""
+    bps = np.geomspace(20.0, 60.0, 8)
+    return dict(name="K128_speedup_8pts", K=128, E0=1.0, points=[(float(b), 9000.0 / float(b)) for b in bps],
+                n=n, seed=0)

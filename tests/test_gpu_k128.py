@@ -165,8 +165,16 @@ def test_deep_accepts_follow_closed_form(T):
     S.close()
     mean = n * math.exp(-L)
     assert st["n_proposals"] == n and abs(st["n_accepted"] - mean) <= 5 * math.sqrt(mean)
-    o = O.replay(O.make_point(K, 1.0, 0.0, 0.0, O.UNIFORM, logM=L), seed, pid, rec["idx"])
+    pt = O.make_point(K, 1.0, 0.0, 0.0, O.UNIFORM, logM=L)
+    o = O.replay(pt, seed, pid, rec["idx"])
     assert np.all(o["accept"]) and np.all(o["lnU"] < -L)
+    # on a prefix the accepted set is exactly the oracle's: the candidates are
+    # the indices whose accept word is in the lowest bucket
+    m = 1 << 27
+    cand, tot = O.tail_scan(K, seed, pid, 0, m, which=2)
+    oc = O.replay(pt, seed, pid, cand)
+    want = set(int(i) for i in cand[oc["accept"]])
+    assert set(int(i) for i in rec["idx"] if int(i) < m) == want
     print("K=128: %d accepts of 2^30 at Delta = -17 (expected %.1f)" % (st["n_accepted"], mean))
 
 
