@@ -246,6 +246,7 @@ def main():
     ap.add_argument("--learn-steps", type=int, default=200)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-k128", action="store_true", help="skip the K = 128 measurement")
+    ap.add_argument("--k128-n", type=int, default=1 << 24, help="K = 128: proposals per point and step")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.impl == "reference":
@@ -411,7 +412,7 @@ def main():
     k128 = None
     if not args.no_k128:
         from paper_2411_16952_gb300 import workloads
-        kw = workloads.speedup_k128()
+        kw = workloads.speedup_k128(args.k128_n)
         kpts = [T.make_point(b, kw["E0"], r, T.PROPOSAL_PAPER, point_id=rank * 8 + p)
                 for p, (b, r) in enumerate(kw["points"])]
         SK = T.Sampler(kw["K"], kpts, sample_capacity=1 << 20, stream=stream)

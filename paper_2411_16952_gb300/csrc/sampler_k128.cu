@@ -8,8 +8,7 @@
 // Philox blocks j = L and L + 32 of every proposal (the stream rule of the
 // one-thread sampler, so both forms draw the same states), writes the scaled
 // pairs (x_m, y_m) to shared memory and keeps its share of |x|^2, S|x|^2,
-// Q|x|^2, u(0), the smallest radius word and the radius-error sums, which
-// warp reductions complete.
+// Q|x|^2, u(0) and the smallest radius word, which warp reductions complete.
 //
 // The double sum, for v_k = x_k - i y_k,
 //   T = sum_{k, l >= 1, k + l <= K} Re(v_k v_l conj(v_{k+l})),
@@ -23,10 +22,14 @@
 // k + l, sums the products of each anti-diagonal i + j = d in packed FP32
 //   P1 = sum (x_k x_l, y_k y_l),  P2 = sum (y_k x_l, x_k y_l)
 // and weights them by v_{k+l} once per anti-diagonal.  Every term passes
-// through fewer than 60 roundings (8 in P, 31 in the tile, 9 over rounds, 5
-// in the warp reduction), below the 2K + 16 chain the decision guard of
-// point_table.cpp allows for, so the guard band and the FP64 pass (k_refine)
-// keep every accept decision exact as in the one-thread sampler.
+// through at most 50 roundings (8 in P, 31 in the tile, 3 over rounds, 5 in
+// the warp reduction, 3 in the scaling), within the chain of 64 the decision
+// guard of point_table.cpp allows the warp form, so the guard band and the
+// FP64 pass (k_refine_warp) keep every accept decision exact.  The radius is
+// rho_log, the full-precision logarithm, whose error is purely relative: the
+// guard needs no per-draw radius terms and is about ten times narrower than
+// it would be with the fast radius, so that about 0.15 % of the draws at
+// K = 128 reach the FP64 pass.
 //
 // Shared-memory layout: proposal q of a warp at word q * kWS, mode m at word
 // m + m/8 (one pad word per block of eight), so that lanes reading the same

@@ -444,6 +444,8 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     }
     h->launch.threads = opt->threads_per_cta ? opt->threads_per_cta : 256;
     h->launch.variant = h->launch.threads == 128 ? 0 : 1;
+    // the warp form (K > 64) fits two 256-thread CTAs per SM at 128 registers
+    if (h->kmax == 128 && h->launch.threads == 256) h->launch.variant = 2;
     if (opt->sir) {
         h->launch.threads = 256;
         h->launch.variant = 1;

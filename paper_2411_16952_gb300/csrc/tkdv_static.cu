@@ -114,7 +114,7 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
         default: triad_kernels_k128(&kt); break;
     }
     const int uni = point->proposal == TKDV_PROPOSAL_UNIFORM ? 1 : 0;
-    const void *fn = kt.main[uni][1];
+    const void *fn = kt.main[uni][kmax == 128 ? 2 : 1];  // warp form: two CTAs per SM
     int sms = 0, nb = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
