@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("accepted samples/sec and proposals/sec at K=32 "
           "(learned+BF16-split vs plain FP32, 1 GB300)")
 L2_FLUSH_BYTES = 256 << 20
+# bytes sampler_stats copies from the device per point (its integer counters,
+# moment sums, 256 histogram and 26 exceedance bins, 128 spectrum sums, 7 SIR
+# sums), plus the 8-byte record count and 4-byte status word per call
+STAT_BYTES_PER_POINT = 8 * (6 + 1 + 4 + 256 + 26 + 1 + 2 + 128 + 1 + 7)
 
 
 def measured_peaks():
@@ -346,9 +350,11 @@ def main():
                "launch": S.launch_config()}
         if fname == headline:
             # end to end through the public API with host buffers: run, then
-            # statistics and accepted records copied to the host every step
+            # statistics and the raw accepted records copied into a pinned
+            # host buffer every step (sampler_stats, sampler_samples)
             S.reset()
             rec_bytes = T.tkdv_record_bytes(K)
+            host_rec = torch.empty((1 << 21) * rec_bytes, dtype=torch.uint8, pin_memory=True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             d2h = 0
@@ -357,9 +363,9 @@ def main():
                 S.reset()
                 S.run(n, seed + 1 + i)
                 sts = S.stats()
-                recs = S.samples(1 << 21)
+                nrec = S.samples(1 << 21, host_dst=host_rec)
                 e2e_acc += sum(s["n_accepted"] for s in sts)
-                d2h += len(recs["idx"]) * rec_bytes + len(sts) * 2304
+                d2h += nrec * rec_bytes + len(sts) * STAT_BYTES_PER_POINT + 12
             e2e_t = time.perf_counter() - t0
             res["e2e"] = {"value": e2e_acc / e2e_t, "unit": "accepted samples/s",
                           "h2d_bytes_per_step": 8 * 2 * len(pts) + 8, "d2h_bytes_per_step": d2h // args.steps}
@@ -459,7 +465,7 @@ def main():
     traffic = None if tr is None or tr[0] is None else tr[0] * props_per_step
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": tr[1] if tr else None,
-            "algorithmic_bytes_per_launch": h["acceptance"] * props_per_step * T.tkdv_record_bytes(K) + 2304 * len(pts),
+            "algorithmic_bytes_per_launch": h["acceptance"] * props_per_step * T.tkdv_record_bytes(K) + STAT_BYTES_PER_POINT * len(pts),
             "ops_per_proposal": ops, "kernel": "k_sample_%s" % form_kind,
             "note": "ideal thread-instruction count per proposal (bench.py alg_ops_per_proposal); peak = "
                     "152 SM x 128 lanes x max SM clock (%s sm_max_mhz)" % peak_src}

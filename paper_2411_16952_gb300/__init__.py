@@ -225,15 +225,25 @@ def sampler_stats(h, n_points):
     return [_stats_dict(out[p]) for p in range(n_points)]
 
 
-def sampler_samples(h, K, max_records, device_dst=None):
+def sampler_samples(h, K, max_records, device_dst=None, host_dst=None):
     """Accepted records: a dict of numpy arrays (host), or, with device_dst (a
     torch uint8 CUDA tensor of max_records * record_bytes), the record count
-    after a device-to-device copy into it."""
+    after a device-to-device copy into it, or, with host_dst (a caller-owned
+    host buffer of at least max_records * record_bytes bytes: a torch uint8
+    CPU tensor, pinned for full copy speed, or a numpy uint8 array), the
+    record count after the raw records were copied into it (no decoding)."""
     n = C.c_uint64()
     rb = tkdv_record_bytes(K)
     if device_dst is not None:
         _check(lib().sampler_samples(h, C.c_void_p(device_dst.data_ptr()), 1, max_records,
                                      C.byref(n)), h)
+        return int(n.value)
+    if host_dst is not None:
+        ptr = host_dst.data_ptr() if hasattr(host_dst, "data_ptr") else host_dst.ctypes.data
+        nbytes = host_dst.numel() if hasattr(host_dst, "numel") else host_dst.nbytes
+        if nbytes < max_records * rb:
+            raise ValueError("host_dst holds %d bytes, %d records need %d" % (nbytes, max_records, max_records * rb))
+        _check(lib().sampler_samples(h, C.c_void_p(ptr), 0, max_records, C.byref(n)), h)
         return int(n.value)
     buf = np.zeros(max(1, max_records) * rb, dtype=np.uint8)
     _check(lib().sampler_samples(h, buf.ctypes.data_as(C.c_void_p), 0, max_records, C.byref(n)), h)
@@ -501,8 +511,8 @@ class Sampler:
     def stats(self):
         return sampler_stats(self.h, self.n_points)
 
-    def samples(self, max_records=1 << 20, device_dst=None):
-        return sampler_samples(self.h, self.K, max_records, device_dst)
+    def samples(self, max_records=1 << 20, device_dst=None, host_dst=None):
+        return sampler_samples(self.h, self.K, max_records, device_dst, host_dst)
 
     def reset(self):
         sampler_reset(self.h)

@@ -307,3 +307,24 @@ def test_k2_acceptance_matches_quadrature(T, prop):
     p = st["n_accepted"] / n
     assert abs(p - acc) < 4 * math.sqrt(acc * (1 - acc) / n), (p, acc)
     assert st["n_envelope_violations"] == 0
+
+
+def test_raw_records_into_host_buffer(T):
+    """sampler_samples into a caller-owned pinned host buffer returns the same
+    raw records the decoding call returns."""
+    import torch
+    K, E0, bp, r = 16, 1.0, 20.0, 75.0
+    lm = envelope(K, E0, bp, r, O.PAPER)
+    S = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, logM=lm)], sample_capacity=1 << 14)
+    S.run(1 << 20, 4)
+    rb = T.tkdv_record_bytes(K)
+    host = torch.empty((1 << 14) * rb, dtype=torch.uint8, pin_memory=True)
+    n = S.samples(1 << 14, host_dst=host)
+    rec = S.samples(1 << 14)
+    with pytest.raises(ValueError):
+        S.samples(1 << 14, host_dst=torch.empty(rb, dtype=torch.uint8))
+    S.close()
+    assert n == len(rec["idx"]) > 0
+    raw = T.decode_records(host[: n * rb].numpy(), K)
+    for key in ("idx", "point", "flags", "H2", "H3", "u0", "delta", "xhat"):
+        assert np.array_equal(raw[key], rec[key]), key
