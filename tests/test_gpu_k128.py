@@ -209,3 +209,39 @@ def test_library_envelope_has_no_violations(T):
     assert st["n_envelope_violations"] == 0 and st["max_delta"] < 0
     print("K=128 library envelope: log M %.4f, acceptance %.3g, max delta %.3f" % (
         st["logM"], st["n_accepted"] / st["n_proposals"], st["max_delta"]))
+
+
+def test_learned_corrections_at_K128(T):
+    """Per-mode log-variance corrections supplied directly (the learned
+    proposal's form; the network itself stops at 64 modes) at K = 128: the
+    oracle's diagonal proposal with the same variances gives the same accept
+    set, and the library's envelope bounds log f/g on every draw of the run."""
+    K, bp, E0, r, seed, pid = 128, 40.0, 1.0, 225.0, 6, 3
+    k = np.arange(1, K + 1)
+    c = 0.3 * np.cos(math.pi * k / K) - 0.1 * np.sin(3 * math.pi * k / K)
+    a = O.alpha_star(K, bp)
+    s2 = (1.0 / (1.0 + a * bp * k * k / K**3)) * np.exp(c)
+    pt0 = O.make_point(K, E0, bp, r, O.DIAG, sigma2=s2)
+    lf = O.replay(pt0, seed, pid, np.arange(2048, dtype=np.uint64))["logfg"]
+    lm = float(lf.max() + np.log(np.mean(np.exp(lf - lf.max()))) - np.log(0.03))
+    pt = O.make_point(K, E0, bp, r, O.DIAG, sigma2=s2, logM=lm)
+    S = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_LEARNED, point_id=pid, logM=lm, log_var_correction=c)],
+                  sample_capacity=1 << 16)
+    _, _, s2_lib = S.point_info(0)
+    assert np.allclose(s2_lib, s2, rtol=1e-13)
+    n = 1 << 17
+    S.run_ranges([0], [n], seed)
+    st = S.stats()[0]
+    rec = S.samples(1 << 16)
+    S.close()
+    total, orec = O.run_accepted(pt, seed, pid, 0, n, cap=1 << 16)
+    excused = compare_accept_sets(rec["idx"], pt, seed, pid, orec["idx"])
+    assert abs(st["n_accepted"] - total) <= excused and total > 1000
+    common = np.isin(rec["idx"], orec["idx"])
+    check_records_against_oracle({kk: v[common] for kk, v in rec.items()}, orec, r, K)
+    S = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_LEARNED, point_id=pid, log_var_correction=c)],
+                  sample_capacity=16)
+    S.run(1 << 22, seed)
+    st = S.stats()[0]
+    S.close()
+    assert st["n_envelope_violations"] == 0 and st["max_delta"] < 0
