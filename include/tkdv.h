@@ -85,6 +85,10 @@ int tkdv_check_radius_error_log(double *max_ratio, uint32_t *worst_word);
 /* ---- H3 forms ------------------------------------------------------------ */
 #define TKDV_H3_TRIAD_F32 0   /* double sum of Eq. (42) on FP32 CUDA cores */
 #define TKDV_H3_GRID_BF16X3 1 /* grid cubature of Eq. (2) as a tensor-core contraction, BF16 hi/lo x3 */
+#define TKDV_H3_AUTO 2        /* the library chooses: the grid form where it exists (sm_10x device, K <= 64,
+                                 not SIR), else the triad form; sampler_autotune then times both and keeps
+                                 the faster (the triad form wins at acceptances above about 0.1, where the
+                                 grid form's per-accept redraw weighs more); sampler_h3_form tells which */
 
 #define TKDV_MAX_POINTS 64
 #define TKDV_HIST_BINS 256
@@ -116,8 +120,8 @@ typedef struct {
                                  K <= 64 one proposal per thread and 65..128 one warp per four proposals
                                  (same stream, same decisions); the grid form and SIR need K <= 64 */
     int h3_mode;              /* TKDV_H3_* */
-    int grid_N;               /* grid points for TKDV_H3_GRID_BF16X3: multiple of 32, > 3K, <= 256;
-                                 0: the smallest such (128 for K = 32) */
+    int grid_N;               /* grid points of the grid form (TKDV_H3_GRID_BF16X3, or TKDV_H3_AUTO with
+                                 K <= 64): multiple of 32, > 3K, <= 256; 0: the smallest such (128 for K = 32) */
     uint64_t sample_capacity; /* accepted records kept per handle (ring; excess is counted, not kept) */
     void *cuda_stream;        /* cudaStream_t to launch on; NULL: the handle makes its own */
     int use_graph;            /* 1: launch each run as one CUDA graph (default), 0: plain launches */
@@ -277,6 +281,20 @@ int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint
    fastest for later runs.  Resets statistics afterwards.  *best_us receives
    the best time (may be NULL). */
 int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us);
+
+/* sampler_h3_form: the H3 form the next run uses, TKDV_H3_TRIAD_F32 or
+   TKDV_H3_GRID_BF16X3 (for a TKDV_H3_AUTO handle: the library's choice).
+   Errors: INVALID_ARG (h NULL). */
+int sampler_h3_form(const tkdv_sampler *h);
+
+/* sampler_batch_run: one call for a batch of points: sampler_create_ex with
+   (points, n_points, opt), budgets[p] proposals of point p from index 0 with
+   `seed`, the statistics of every point into out (n_points entries, host,
+   caller-owned), then sampler_destroy.  Errors as sampler_create_ex,
+   sampler_run_budgets and sampler_stats; the message is in
+   sampler_last_error(NULL). */
+int sampler_batch_run(const tkdv_point *points, int n_points, const tkdv_options *opt, const uint64_t *budgets,
+                      uint64_t seed, tkdv_stats *out);
 
 /* sampler_launch_config: the launch shape of the next run. */
 int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk);

@@ -26,7 +26,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "NO_ALPHA", -3: "CUDA", -4: "OOM", -5: "TIMEOUT
           -6: "UNSUPPORTED", -7: "ENVELOPE", -8: "TOO_LARGE"}
 STATIC_MAX_PROPOSALS = 262144
 PROPOSAL_UNIFORM, PROPOSAL_PAPER, PROPOSAL_LEARNED = 0, 1, 2
-H3_TRIAD_F32, H3_GRID_BF16X3 = 0, 1
+H3_TRIAD_F32, H3_GRID_BF16X3, H3_AUTO = 0, 1, 2
 MAX_POINTS = 64
 HIST_BINS = 256
 N_EXCEED = 25
@@ -38,7 +38,7 @@ EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler
             "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
             "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static",
             "sampler_set_trace", "tkdv_check_radius_error", "tkdv_check_radius_error_log",
-            "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
+            "sampler_h3_form", "sampler_batch_run", "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
             "tkdv_mlp_features", "tkdv_mlp_get_params", "tkdv_mlp_set_params", "tkdv_mlp_infer",
             "tkdv_mlp_set_data", "tkdv_mlp_set_data_records", "tkdv_mlp_rows", "tkdv_mlp_step"]
 MLP_NPARAM = 8640
@@ -121,6 +121,9 @@ def lib():
             L.sampler_replay.argtypes = [vp, i, u64p, u64, u64, dp]
             L.sampler_autotune.argtypes = [vp, u64, dp]
             L.sampler_launch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_uint32)]
+            L.sampler_h3_form.argtypes = [vp]
+            L.sampler_batch_run.argtypes = [C.POINTER(tkdv_point), i, C.POINTER(tkdv_options), u64p, u64,
+                                            C.POINTER(tkdv_stats)]
             L.sampler_last_error.argtypes = [vp]
             L.sampler_last_error.restype = C.c_char_p
             L.sampler_destroy.argtypes = [vp]
@@ -293,6 +296,26 @@ def sampler_autotune(h, calib_proposals):
     us = C.c_double()
     _check(lib().sampler_autotune(h, calib_proposals, C.byref(us)), h)
     return us.value
+
+
+def sampler_h3_form(h):
+    """H3 form of the next run: H3_TRIAD_F32 or H3_GRID_BF16X3."""
+    f = lib().sampler_h3_form(h)
+    _check(f if f < 0 else TKDV_OK, h)
+    return f
+
+
+def sampler_batch_run(points, options, budgets, seed):
+    """One call for a batch of points (create, run the budgets from index 0,
+    statistics, destroy): a list of statistics dicts."""
+    arr = (tkdv_point * len(points))(*points)
+    b = np.ascontiguousarray(np.asarray(budgets, dtype=np.uint64))
+    if b.shape != (len(points),):
+        raise ValueError("one budget per point")
+    out = (tkdv_stats * len(points))()
+    _check(lib().sampler_batch_run(arr, len(points), C.byref(options), b.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                   seed, out))
+    return [_stats_dict(out[p]) for p in range(len(points))]
 
 
 def sampler_launch_config(h):
@@ -478,6 +501,24 @@ def make_point(beta_p, E0, r, proposal=PROPOSAL_PAPER, point_id=0, logM=None, lo
     return p
 
 
+def make_options(K, h3_mode=H3_TRIAD_F32, grid_N=0, sample_capacity=1 << 20, stream=None, use_graph=True,
+                 ctas_per_sm=0, threads_per_cta=0, sir=False):
+    """tkdv_options of a handle (include/tkdv.h)."""
+    o = tkdv_options()
+    o.K, o.h3_mode, o.grid_N = K, h3_mode, grid_N
+    o.sample_capacity = sample_capacity
+    if stream is None:
+        o.cuda_stream = None  # the library makes its own stream
+    else:
+        handle = int(getattr(stream, "cuda_stream", stream))
+        # handle 0 is the legacy default stream; pass cudaStreamLegacy (0x1) for it
+        o.cuda_stream = C.c_void_p(handle if handle != 0 else 1)
+    o.use_graph = 1 if use_graph else 0
+    o.ctas_per_sm, o.threads_per_cta = ctas_per_sm, threads_per_cta
+    o.sir = 1 if sir else 0
+    return o
+
+
 class Sampler:
     """One handle of the C library (several parameter points, one K)."""
 
@@ -485,18 +526,7 @@ class Sampler:
                  stream=None, use_graph=True, ctas_per_sm=0, threads_per_cta=0, sir=False):
         self.K = K
         self.n_points = len(points)
-        o = tkdv_options()
-        o.K, o.h3_mode, o.grid_N = K, h3_mode, grid_N
-        o.sample_capacity = sample_capacity
-        if stream is None:
-            o.cuda_stream = None  # the library makes its own stream
-        else:
-            handle = int(getattr(stream, "cuda_stream", stream))
-            # handle 0 is the legacy default stream; pass cudaStreamLegacy (0x1) for it
-            o.cuda_stream = C.c_void_p(handle if handle != 0 else 1)
-        o.use_graph = 1 if use_graph else 0
-        o.ctas_per_sm, o.threads_per_cta = ctas_per_sm, threads_per_cta
-        o.sir = 1 if sir else 0
+        o = make_options(K, h3_mode, grid_N, sample_capacity, stream, use_graph, ctas_per_sm, threads_per_cta, sir)
         self.h = sampler_create_ex(points, o)
 
     def run(self, n_proposals, seed):
@@ -557,6 +587,9 @@ class Sampler:
 
     def launch_config(self):
         return sampler_launch_config(self.h)
+
+    def h3_form(self):
+        return sampler_h3_form(self.h)
 
     def close(self):
         if self.h:

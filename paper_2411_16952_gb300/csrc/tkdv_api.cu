@@ -24,6 +24,7 @@ struct Launch {
     int threads = 256;
     int ctas = 0;
     int variant = 1;  // triad form: index into TriadKernels::main[][variant]
+    int form = TKDV_H3_TRIAD_F32;
 };
 
 }  // namespace
@@ -34,7 +35,9 @@ struct tkdv_sampler {
     std::vector<tkdv_point> pts;
     std::vector<double> alpha, logM;
     std::vector<std::vector<double>> sigma2;
-    std::vector<PointConst> pc;
+    std::vector<PointConst> pc;            // table of the current form (uploaded)
+    std::vector<PointConst> pc_triad, pc_grid;  // both forms' tables (the grid guard is wider)
+    bool grid_ok = false;                  // the grid form's resources exist (grid mode, or AUTO on sm_10x)
     std::vector<unsigned long long> next_idx;
     bool all_uniform = false;
     int device = 0, num_sms = 0;
@@ -142,13 +145,30 @@ int build_point(tkdv_sampler *h, int p, std::string &msg) {
     h->logM[p] = lm;
     h->sigma2[p] = s2;
 
-    PointConst c;
-    fill_point_const(K, q, s2.data(), lm, h->opt.h3_mode == TKDV_H3_GRID_BF16X3, c);
-    h->pc[p] = c;
+    fill_point_const(K, q, s2.data(), lm, false, h->pc_triad[p]);
+    fill_point_const(K, q, s2.data(), lm, true, h->pc_grid[p]);
+    h->pc[p] = h->opt.h3_mode == TKDV_H3_GRID_BF16X3 ? h->pc_grid[p] : h->pc_triad[p];
     return TKDV_OK;
 }
 
-bool is_grid(const tkdv_sampler *h) { return h->opt.h3_mode == TKDV_H3_GRID_BF16X3; }
+bool is_grid(const tkdv_sampler *h) { return h->launch.form == TKDV_H3_GRID_BF16X3; }
+
+// Switch the form of the next runs (TKDV_H3_AUTO handles): its point table
+// and its default launch shape; the graph is rebuilt on the next run.
+int set_form(tkdv_sampler *h, int form) {
+    h->launch.form = form;
+    h->pc = form == TKDV_H3_GRID_BF16X3 ? h->pc_grid : h->pc_triad;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(h->d_pts, h->pc.data(), sizeof(PointConst) * h->n_points, cudaMemcpyHostToDevice));
+    if (form == TKDV_H3_GRID_BF16X3) {
+        h->launch.threads = 128;
+        h->launch.variant = 0;
+    } else {
+        h->launch.threads = 256;
+        h->launch.variant = h->kmax == 128 ? 2 : 1;
+    }
+    return TKDV_OK;
+}
 
 const void *main_fn(const tkdv_sampler *h, int variant) {
     const int uni = h->all_uniform ? 1 : 0;
@@ -288,7 +308,7 @@ int enqueue(tkdv_sampler *h) {
     const int uni = h->all_uniform ? 1 : 0;
     if (h->opt.use_graph) {
         if (!h->exec || h->graph_launch.ctas != h->launch.ctas || h->graph_launch.threads != h->launch.threads ||
-            h->graph_launch.variant != h->launch.variant) {
+            h->graph_launch.variant != h->launch.variant || h->graph_launch.form != h->launch.form) {
             int rc = build_graph(h);
             if (rc) return rc;
         }
@@ -381,10 +401,13 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (n_points < 1 || n_points > kMaxPoints)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "n_points must be in 1..64");
     if (opt->K < 1 || opt->K > kKMax) return fail(nullptr, TKDV_ERR_INVALID_ARG, "K must be in 1..128");
-    if (opt->h3_mode != TKDV_H3_TRIAD_F32 && opt->h3_mode != TKDV_H3_GRID_BF16X3)
+    if (opt->h3_mode != TKDV_H3_TRIAD_F32 && opt->h3_mode != TKDV_H3_GRID_BF16X3 && opt->h3_mode != TKDV_H3_AUTO)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "unknown h3_mode");
+    // AUTO: the grid form is a candidate where it exists (K <= 64, not SIR)
+    const bool want_grid = opt->h3_mode == TKDV_H3_GRID_BF16X3 ||
+                           (opt->h3_mode == TKDV_H3_AUTO && opt->K <= 64 && !opt->sir);
     int gridN = 0;
-    if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
+    if (want_grid) {
         gridN = opt->grid_N ? opt->grid_N : ((3 * opt->K + 1 + 31) / 32) * 32;
         if (gridN % 32 != 0 || gridN <= 3 * opt->K || gridN > 256)
             return fail(nullptr, TKDV_ERR_INVALID_ARG,
@@ -393,7 +416,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (opt->threads_per_cta != 0 && opt->threads_per_cta != 128 && opt->threads_per_cta != 256)
         return fail(nullptr, TKDV_ERR_INVALID_ARG, "threads_per_cta must be 0, 128 or 256");
     if (opt->sir != 0 && opt->sir != 1) return fail(nullptr, TKDV_ERR_INVALID_ARG, "sir must be 0 or 1");
-    if (opt->sir && opt->h3_mode != TKDV_H3_TRIAD_F32)
+    if (opt->sir && opt->h3_mode == TKDV_H3_GRID_BF16X3)
         return fail(nullptr, TKDV_ERR_UNSUPPORTED, "SIR runs use the triad form");
     if (opt->sir && opt->K > 64) return fail(nullptr, TKDV_ERR_UNSUPPORTED, "SIR runs need K <= 64");
     if (opt->sir)
@@ -411,6 +434,8 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     h->logM.assign(n_points, 0.0);
     h->sigma2.assign(n_points, {});
     h->pc.assign(n_points, PointConst{});
+    h->pc_triad.assign(n_points, PointConst{});
+    h->pc_grid.assign(n_points, PointConst{});
     h->next_idx.assign(n_points, 0ull);
     h->all_uniform = true;
     for (int p = 0; p < n_points; ++p) {
@@ -450,19 +475,29 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
         h->launch.threads = 256;
         h->launch.variant = 1;
     }
-    if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
+    bool grid_here = want_grid;
+    if (want_grid) {
         int major = 0;
         e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
         if (e != cudaSuccess || major != 10) {
-            h->err = "the tensor-core grid form needs an sm_10x (tcgen05) device";
-            return bail(TKDV_ERR_UNSUPPORTED);
+            if (opt->h3_mode == TKDV_H3_GRID_BF16X3) {
+                h->err = "the tensor-core grid form needs an sm_10x (tcgen05) device";
+                return bail(TKDV_ERR_UNSUPPORTED);
+            }
+            grid_here = false;  // AUTO on another device: the triad form only
         }
+    }
+    if (grid_here) {
         if (h->K <= 16)
             grid_kernels_k16(&h->kg);
         else if (h->K <= 32)
             grid_kernels_k32(&h->kg);
         else
             grid_kernels_k64(&h->kg);
+        h->grid_ok = true;
+        h->launch.form = TKDV_H3_GRID_BF16X3;
+        h->launch.variant = 0;
+        h->pc = h->pc_grid;
         h->launch.threads = 128;
         const size_t btile = (size_t)gridN * h->kg.ka * 2, atile = (size_t)128 * h->kg.ka * 2;
         h->dyn_smem = 2 * btile + (size_t)h->kg.nwg * 2 * atile + 1024;
@@ -738,7 +773,6 @@ int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint
 
 int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us) {
     if (!h || calib_proposals == 0) return TKDV_ERR_INVALID_ARG;
-    const int uni = h->all_uniform ? 1 : 0;
     const int saved_graph = h->opt.use_graph;
     h->opt.use_graph = 0;
     std::vector<unsigned long long> i0(h->n_points, 1ull << 62), c(h->n_points, calib_proposals);
@@ -747,45 +781,75 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
     CK(cudaEventCreate(&e1));
     Launch best = h->launch;
     float best_ms = 1e30f;
-    std::vector<int> var_list = {0, 1, 2};
-    if (is_grid(h)) var_list = {0};
-    if (h->opt.sir) var_list = {1};
-    (void)uni;
-    for (int var : var_list) {
-        const int thr = is_grid(h) ? 128 : kTriadVariantThreads[var];
-        int nb = 0;
-        int rc0 = max_ctas_per_sm(h, var, thr, &nb);
-        if (rc0) return rc0;
-        for (int per = 1; per <= nb; ++per) {
-            h->launch.threads = thr;
-            h->launch.variant = var;
-            h->launch.ctas = per * h->num_sms;
-            float ms_best = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                CK(cudaEventRecord(e0, h->stream));
-                int rc = run_ranges(h, i0.data(), c.data(), 0x5EEDull + rep);
-                if (rc) return rc;
-                CK(cudaEventRecord(e1, h->stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0) ms_best = std::min(ms_best, ms);
-            }
-            if (std::getenv("TKDV_AUTOTUNE_LOG"))
-                std::fprintf(stderr, "tkdv autotune: variant %d threads %d ctas/SM %d -> %.3f ms\n", var, thr, per,
-                             (double)ms_best);
-            if (ms_best < best_ms) {
-                best_ms = ms_best;
-                best = h->launch;
+    // TKDV_H3_AUTO with both forms available: time both and keep the faster
+    std::vector<int> forms = {h->launch.form};
+    if (h->opt.h3_mode == TKDV_H3_AUTO && h->grid_ok) forms = {TKDV_H3_GRID_BF16X3, TKDV_H3_TRIAD_F32};
+    for (int form : forms) {
+        if (form != h->launch.form) {
+            const int rcf = set_form(h, form);
+            if (rcf) return rcf;
+        }
+        std::vector<int> var_list = {0, 1, 2};
+        if (is_grid(h)) var_list = {0};
+        if (h->opt.sir) var_list = {1};
+        for (int var : var_list) {
+            const int thr = is_grid(h) ? 128 : kTriadVariantThreads[var];
+            int nb = 0;
+            const int rc0 = max_ctas_per_sm(h, var, thr, &nb);
+            if (rc0) return rc0;
+            for (int per = 1; per <= nb; ++per) {
+                h->launch.threads = thr;
+                h->launch.variant = var;
+                h->launch.ctas = per * h->num_sms;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    CK(cudaEventRecord(e0, h->stream));
+                    const int rc = run_ranges(h, i0.data(), c.data(), 0x5EEDull + rep);
+                    if (rc) return rc;
+                    CK(cudaEventRecord(e1, h->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) ms_best = std::min(ms_best, ms);
+                }
+                if (std::getenv("TKDV_AUTOTUNE_LOG"))
+                    std::fprintf(stderr, "tkdv autotune: form %s variant %d threads %d ctas/SM %d -> %.3f ms\n",
+                                 is_grid(h) ? "grid" : "triad", var, thr, per, (double)ms_best);
+                if (ms_best < best_ms) {
+                    best_ms = ms_best;
+                    best = h->launch;
+                }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best.form != h->launch.form) {
+        const int rcf = set_form(h, best.form);
+        if (rcf) return rcf;
+    }
     h->launch = best;
     h->opt.use_graph = saved_graph;
     if (best_us) *best_us = best_ms * 1000.0;
     return sampler_reset(h);
+}
+
+int sampler_h3_form(const tkdv_sampler *h) {
+    if (!h) return TKDV_ERR_INVALID_ARG;
+    return h->launch.form;
+}
+
+int sampler_batch_run(const tkdv_point *points, int n_points, const tkdv_options *opt, const uint64_t *budgets,
+                      uint64_t seed, tkdv_stats *out) {
+    if (!budgets || !out) return fail(nullptr, TKDV_ERR_INVALID_ARG, "budgets/out NULL");
+    tkdv_sampler *h = nullptr;
+    int rc = sampler_create_ex(points, n_points, opt, &h);
+    if (rc) return rc;
+    rc = sampler_run_budgets(h, budgets, seed);
+    if (!rc) rc = sampler_stats(h, out, n_points);
+    if (rc) g_create_error = h->err;
+    sampler_destroy(h);
+    return rc;
 }
 
 int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk) {

@@ -59,3 +59,31 @@ def merge_stats(stats, group=None):
         d["max_delta"] = float(mx[p])
         out.append(d)
     return out
+
+
+def gather_records(raw, rec_bytes, group=None):
+    """Concatenate the accepted records of all ranks (torch.distributed
+    all-gather), in rank order, on every rank.  raw: this rank's records as
+    a flat uint8 array of whole records (e.g. a buffer filled by
+    Sampler.samples(host_dst=...), cut to n * rec_bytes); rec_bytes:
+    tkdv_record_bytes(K).  Host tensors under gloo, device tensors under
+    NCCL; one exchange after the runs, none on the sampling path."""
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" \
+        else torch.device("cpu")
+    raw = np.ascontiguousarray(np.asarray(raw, dtype=np.uint8))
+    if len(raw) % rec_bytes:
+        raise ValueError("raw holds %d bytes, not whole %d-byte records" % (len(raw), rec_bytes))
+    n = len(raw) // rec_bytes
+    world = dist.get_world_size(group)
+    cnt = torch.tensor([n], dtype=torch.int64, device=dev)
+    cnts = [torch.zeros_like(cnt) for _ in range(world)]
+    dist.all_gather(cnts, cnt, group=group)
+    counts = [int(c.item()) for c in cnts]
+    buf = torch.zeros(max(1, max(counts)) * rec_bytes, dtype=torch.uint8, device=dev)
+    if n:
+        buf[: n * rec_bytes] = torch.from_numpy(raw).to(dev)
+    bufs = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(bufs, buf, group=group)
+    return np.concatenate([b[: c * rec_bytes].cpu().numpy() for b, c in zip(bufs, counts)])

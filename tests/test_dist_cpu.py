@@ -22,7 +22,22 @@ def _as_lib_stats(st):
     return {"n_proposals": st["n_prop"], "n_accepted": st["n_acc"], "n_near_threshold": st["n_near"],
             "n_refined": 0, "n_envelope_violations": st["n_viol"], "n_dropped": 0, "n_fallback": 0,
             "hist": st["hist"], "exceed": st["exceed"], "sum_u0": st["sum_u0"], "max_delta": st["max_delta"],
-            "spectrum": np.concatenate([st["spectrum"], np.zeros(64 - len(st["spectrum"]))])}
+            "spectrum": np.concatenate([st["spectrum"], np.zeros(D.KMAX - len(st["spectrum"]))])}
+
+
+def _encode(rec, K, point):
+    """The library's record layout (include/tkdv.h: idx, point, flags, H2, H3,
+    u0, log f/(Mg), xhat) of oracle records, as raw bytes."""
+    import paper_2411_16952_gb300 as T
+    rb = T.tkdv_record_bytes(K)
+    n = len(rec["idx"])
+    out = np.zeros((n, rb), dtype=np.uint8)
+    out[:, 0:8] = rec["idx"].astype(np.uint64).reshape(n, 1).view(np.uint8)
+    out[:, 8:12] = np.full((n, 1), point, dtype=np.uint32).view(np.uint8)
+    for j, key in enumerate(("H2", "H3", "u0", "delta")):
+        out[:, 16 + 4 * j:20 + 4 * j] = rec[key].astype(np.float32).reshape(n, 1).view(np.uint8)
+    out[:, 32:32 + 8 * K] = rec["xhat"][:, :2 * K].astype(np.float32).view(np.uint8)
+    return out.reshape(-1)
 
 
 def _worker(rank, world, port, q):
@@ -39,8 +54,12 @@ def _worker(rank, world, port, q):
     pid = D.rank_point_id(rank, 1, 2)
     st2 = O.run_stats(pt, 7, pid, 0, 50_000, 1)
     merged = D.merge_stats([_as_lib_stats(st), _as_lib_stats(st2)])
+    # accepted records of the shards, gathered in rank order
+    import paper_2411_16952_gb300 as T
+    _, rec = O.run_accepted(pt, 7, 3, start, count, cap=1 << 16)
+    allrec = D.gather_records(_encode(rec, K, 0), T.tkdv_record_bytes(K))
     if rank == 0:
-        q.put(merged)
+        q.put((merged, allrec))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -54,7 +73,7 @@ def test_two_ranks_merge_to_one_run():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    merged = q.get(timeout=300)
+    merged, allrec = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -71,6 +90,15 @@ def test_two_ranks_merge_to_one_run():
     assert merged[0]["max_delta"] == one["max_delta"]
     # rank-specific streams: point ids 1 and 3 are different draws
     assert merged[1]["n_proposals"] == 100_000
+    # the gathered records are the one run's accepted draws, rank 0's first
+    import paper_2411_16952_gb300 as T
+    g = T.decode_records(allrec, K)
+    total, rec = O.run_accepted(pt, 7, 3, 0, n, cap=1 << 16)
+    assert len(g["idx"]) == total == merged[0]["n_accepted"]
+    assert np.array_equal(np.sort(g["idx"]), np.sort(rec["idx"]))
+    assert np.all(np.diff(g["idx"][g["idx"] < D.shard_range(n, 1, 2)[0]].astype(np.int64)) > 0)
+    o = np.argsort(rec["idx"])
+    assert np.array_equal(g["xhat"][np.argsort(g["idx"])], rec["xhat"][o][:, :2 * K].astype(np.float32))
 
 
 def test_shard_range_covers_exactly():

@@ -8,7 +8,7 @@ per-mode spectrum statistic.
 """
 import pytest
 
-from test_matching_cpu import mean_S_closed
+from test_matching_cpu import mean_S_closed, mean_S_stable
 
 pytestmark = pytest.mark.gpu
 
@@ -33,3 +33,18 @@ def test_bisection_recovers_closed_form_beta(T, h3_mode, grid_N):
     # per candidate ~4e6 accepted fields: mean S to ~2e-3, slope ~ -0.3 per unit beta'
     assert abs(res["beta"] - beta_true) < 0.05, res["beta"]
     print("bisection (h3_mode %d): beta' = %.4f, bracket %s" % (h3_mode, res["beta"], res["bracket"]))
+
+
+def test_bisection_K64_grid256(T):
+    """The 64-mode configuration of the downstream search: K = 64, the grid
+    form with N = 256 points, 16 candidates per step in one launch.  The
+    target is the closed-form mean of S at beta' = 40 (matrix-exponential
+    form, pinned against the explicit sum on the CPU)."""
+    from paper_2411_16952_gb300 import matching as MT
+    K, beta_true = 64, 40.0
+    res = MT.bisect_beta(K, 1.0, 0.0, MT.mean_S, mean_S_stable(K, beta_true), 20.0, 80.0, n_candidates=16,
+                         n_steps=3, proposals_per_candidate=1 << 22, seed=9, h3_mode=T.H3_GRID_BF16X3, grid_N=256)
+    # mean S falls by about 4.8 per unit beta' here; its sampling error per
+    # candidate (about 4e6 accepted fields) is below 0.1
+    assert abs(res["beta"] - beta_true) < 0.15, res["beta"]
+    print("K = 64, N = 256 bisection: beta' = %.4f, bracket %s" % (res["beta"], res["bracket"]))

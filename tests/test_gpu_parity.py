@@ -328,3 +328,55 @@ def test_raw_records_into_host_buffer(T):
     raw = T.decode_records(host[: n * rb].numpy(), K)
     for key in ("idx", "point", "flags", "H2", "H3", "u0", "delta", "xhat"):
         assert np.array_equal(raw[key], rec[key]), key
+
+
+def test_auto_form_takes_the_exact_decisions_of_both_forms(T):
+    """TKDV_H3_AUTO: the grid form before autotuning (K <= 64 on this device),
+    the faster form after it; every form accepts the same draws.  K = 128 and
+    SIR runs take the triad form."""
+    K, E0, bp, r, n, seed = 16, 1.0, 20.0, 75.0, 1 << 21, 8
+    pts = [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=2, logM=envelope(K, E0, bp, r, O.PAPER))]
+    sets, views = {}, {}
+    for mode in (T.H3_TRIAD_F32, T.H3_GRID_BF16X3, T.H3_AUTO):
+        S = T.Sampler(K, pts, h3_mode=mode, sample_capacity=1 << 16)
+        if mode == T.H3_AUTO:
+            assert S.h3_form() == T.H3_GRID_BF16X3
+            S.autotune(1 << 20)
+            assert S.h3_form() in (T.H3_TRIAD_F32, T.H3_GRID_BF16X3)
+        S.run_ranges([0], [n], seed)
+        st = S.stats()[0]
+        sets[mode] = set(S.samples(1 << 16)["idx"].tolist())
+        views[mode] = (st["n_proposals"], st["n_accepted"], st["n_envelope_violations"])
+        S.close()
+    pt = O.make_point(K, E0, bp, r, O.PAPER, logM=pts[0].logM)
+    for mode in (T.H3_GRID_BF16X3, T.H3_AUTO):
+        diff = sorted(sets[mode] ^ sets[T.H3_TRIAD_F32])
+        if diff:
+            assert O.replay(pt, seed, 2, np.array(diff, dtype=np.uint64))["near"].all()
+    assert views[T.H3_AUTO][0] == n
+    S = T.Sampler(128, [T.make_point(60.0, 1.0, 150.0, T.PROPOSAL_PAPER, logM=10.0)], h3_mode=T.H3_AUTO)
+    assert S.h3_form() == T.H3_TRIAD_F32
+    S.close()
+    S = T.Sampler(16, [T.make_point(20.0, 1.0, 75.0, T.PROPOSAL_PAPER, logM=envelope(K, E0, bp, r, O.PAPER))],
+                  h3_mode=T.H3_AUTO, sir=True)
+    assert S.h3_form() == T.H3_TRIAD_F32
+    S.close()
+
+
+def test_batch_run_equals_a_handle(T):
+    """sampler_batch_run (create, run, statistics, destroy in one call) gives
+    the statistics of a handle run on the same points, budgets and seed."""
+    K = 16
+    cfg = [(20.0, 1.0, 75.0, O.PAPER, 0, 300_001), (40.0, 0.7, 30.0, O.PAPER, 1, 100_000)]
+    pts = [T.make_point(bp, E0, r, tprop(T, prop), point_id=pid, logM=envelope(K, E0, bp, r, prop))
+           for bp, E0, r, prop, pid, _ in cfg]
+    budgets = [c[-1] for c in cfg]
+    out = T.sampler_batch_run(pts, T.make_options(K, sample_capacity=16), budgets, 5)
+    S = T.Sampler(K, pts, sample_capacity=16)
+    S.run_budgets(budgets, 5)
+    ref = S.stats()
+    S.close()
+    for p in range(len(cfg)):
+        assert int_view(out[p]) == int_view(ref[p]), p
+    with pytest.raises(T.TkdvError):
+        T.sampler_batch_run(pts, T.make_options(200), budgets, 5)

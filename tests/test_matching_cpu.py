@@ -24,6 +24,24 @@ def mean_S_closed(K, bp):
     return (K - 1) / a + float(np.sum(k * k * e) / np.sum(e))
 
 
+def mean_S_stable(K, bp):
+    """The same mean for large K: Z(a) = (K-1)! times the divided difference
+    of exp at the nodes -a k^2 (Hermite-Genocchi), taken as the corner entry
+    of the exponential of the bidiagonal matrix with those nodes on the
+    diagonal and ones above it (Opitz's theorem), which avoids the
+    cancellation of the explicit sum; mean S = -d ln Z / da by central
+    differences."""
+    sl = pytest.importorskip("scipy.linalg")
+
+    def lnZ(a):
+        x = -a * np.arange(1, K + 1, dtype=np.float64) ** 2
+        return math.log(sl.expm(np.diag(x) + np.diag(np.ones(K - 1), 1))[0, K - 1]) + math.lgamma(K)
+
+    a = bp / K**2
+    h = 1e-5 * a
+    return -(lnZ(a + h) - lnZ(a - h)) / (2 * h)
+
+
 def fake_batch(K, noise=0.0, seed=0):
     rng = np.random.default_rng(seed)
 
@@ -81,3 +99,14 @@ def test_bisection_rejects_unbracketed_target():
         MT.bisect_beta(K, 1.0, 0.0, MT.mean_S, mean_S_closed(K, 80.0), 10.0, 60.0, run_batch=fake_batch(K))
     with pytest.raises(ValueError):
         MT.bisect_beta(K, 1.0, 0.0, MT.mean_S, 1.0, 60.0, 10.0, run_batch=fake_batch(K))
+
+
+def test_stable_closed_form_matches_explicit_sum():
+    """The matrix-exponential form of the r = 0 mean of S equals the explicit
+    divided-difference sum where the latter is still accurate (K <= 16), and
+    stays between the extreme values of S at K = 64."""
+    for K, bp in [(8, 30.0), (8, 60.0), (16, 20.0), (16, 80.0)]:
+        assert abs(mean_S_stable(K, bp) - mean_S_closed(K, bp)) < 1e-9 * mean_S_closed(K, bp)
+    K = 64
+    vals = [mean_S_stable(K, bp) for bp in (20.0, 40.0, 80.0)]
+    assert 1.0 < vals[2] < vals[1] < vals[0] < (K + 1) * (2 * K + 1) / 6.0  # below the uniform mean
