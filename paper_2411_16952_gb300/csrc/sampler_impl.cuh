@@ -411,6 +411,20 @@ __device__ __noinline__ void eval64(const PointConst *P, unsigned long long idx,
     }
 }
 
+// Write the 32-byte header of one accepted record (the projected state follows it).
+__device__ __forceinline__ void write_header(unsigned char *rec, unsigned long long idx, uint32_t point,
+                                             uint32_t flags, float H2, float H3, float u0, float delta) {
+    *reinterpret_cast<unsigned long long *>(rec) = idx;
+    uint32_t *h = reinterpret_cast<uint32_t *>(rec + 8);
+    h[0] = point;
+    h[1] = flags;
+    float *f = reinterpret_cast<float *>(rec + 16);
+    f[0] = H2;
+    f[1] = H3;
+    f[2] = u0;
+    f[3] = delta;
+}
+
 // Write one accepted record.
 template <int KMAX>
 __device__ __forceinline__ void write_record(unsigned char *rec, unsigned long long idx, uint32_t point,
@@ -488,6 +502,11 @@ __device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long lo
 }
 
 // ---- the persistent sampler ----------------------------------------------
+// Floats between two threads' slabs of the accept hand-off (2 KMAX + 4: the
+// 16-byte pad moves consecutive lanes' vector stores to different banks).
+template <int KMAX>
+__host__ __device__ constexpr int xfer_stride() { return 2 * KMAX + 4; }
+
 template <int KMAX, bool UNIF, int NT, int MINB, bool SIR = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_sample_triad(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1) {
@@ -500,6 +519,10 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ uint32_t s_maxd;
     __shared__ uint32_t s_chunk;
     __shared__ float s_sig[KMAX], s_act[KMAX];
+    // dynamic: per thread, its accepted draw's scaled state (x | y), padded
+    // (kXferStride floats apart, so that the lanes' vector stores spread over
+    // the banks); absent in the SIR form
+    extern __shared__ __align__(16) float s_xfer[];
 
     const int tid = threadIdx.x, lane = tid & 31;
     for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
@@ -614,26 +637,67 @@ __global__ void __launch_bounds__(NT, MINB)
                     atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
                 }
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                unsigned char *rec = nullptr;
+                bool redo = false;
                 if (acc) {
                     const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
-                    unsigned char *rec = nullptr;
                     if (slot < B.ring_cap)
                         rec = B.ring + slot * B.rec_bytes;
                     else
                         atomicAdd(&s_cnt[2], 1u);
-                    if (dr.rrmax * f.inv > kOutputRr) {
+                    redo = dr.rrmax * f.inv > kOutputRr;
+                    if (redo) {
                         // a radius of the series range: outputs from rho_acc
                         emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
                                                   s_spec, rec);
                     } else {
                         const float u0 = sc.u0s * dr.u0raw * f.inv;
                         tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
-                        tally_spectrum<KMAX>(s_spec, dr.x, dr.y, f.inv * f.inv, sc.K);
-                        if (rec)
-                            write_record<KMAX>(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta,
-                                               dr.x, dr.y, f.inv, sc.K);
+                        if (rec) write_header(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta);
                     }
                 }
+                // Spectrum and projected state of the other accepted draws: each
+                // hands its (x | y) to its warp through shared memory (one
+                // straight run of vector stores), then the warp takes the draws
+                // one at a time, lane m mode m.  So the hot loop carries no
+                // unrolled per-mode tally or record stores (which, executed in a
+                // quarter of the iterations at 1 % acceptance, cost the loop its
+                // instruction cache), the atomics do not contend and the record
+                // writes are coalesced.
+                const bool coop = acc && !redo;
+                if (coop) {
+                    float *xo = s_xfer + (size_t)tid * xfer_stride<KMAX>();
+#pragma unroll
+                    for (int m = 0; m < KMAX; m += 4) {
+                        *reinterpret_cast<float4 *>(xo + m) = make_float4(dr.x[m], dr.x[m + 1], dr.x[m + 2], dr.x[m + 3]);
+                        *reinterpret_cast<float4 *>(xo + KMAX + m) =
+                            make_float4(dr.y[m], dr.y[m + 1], dr.y[m + 2], dr.y[m + 3]);
+                    }
+                }
+                unsigned mq = __ballot_sync(0xffffffffu, coop);
+                __syncwarp();
+                while (mq) {
+                    const int L = __ffs(mq) - 1;
+                    mq &= mq - 1;
+                    const float *xf = s_xfer + (size_t)((tid & ~31) + L) * xfer_stride<KMAX>();
+                    const float inv = __shfl_sync(0xffffffffu, f.inv, L);
+                    float *xh = reinterpret_cast<float *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rec), L));
+                    const float sc2 = (inv * inv) * kSpecScale;
+#pragma unroll
+                    for (int m0 = 0; m0 < KMAX; m0 += 32) {
+                        const int m = m0 + lane;
+                        if (m < sc.K) {
+                            const float x = xf[m], y = xf[KMAX + m];
+                            atomicAdd(&s_spec[m], (unsigned long long)__float2ull_rn(fmaf(x, x, y * y) * sc2));
+                            if (xh) {
+                                xh[8 + m] = x * inv;
+                                xh[8 + sc.K + m] = y * inv;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();  // the slabs are rewritten in the next iteration
             }
         }
         // chunk done: flush this CTA's partials into the point's StatBlock
@@ -856,6 +920,7 @@ void fill_triad_kernels(TriadKernels *t) {
     t->replay[0] = (const void *)k_replay<KMAX, false>;
     t->replay[1] = (const void *)k_replay<KMAX, true>;
     t->replay_per_block = 128;
+    t->xfer_bytes_per_thread = (int)(xfer_stride<KMAX>() * sizeof(float));
 }
 
 }  // namespace tkdv

@@ -697,6 +697,7 @@ void triad_kernels_k128(TriadKernels *t) {
     t->replay[0] = (const void *)k_replay_warp<false>;
     t->replay[1] = (const void *)k_replay_warp<true>;
     t->replay_per_block = 32 * kReplayWarps / 32 * kWQ;
+    t->xfer_bytes_per_thread = 0;
 }
 
 }  // namespace tkdv

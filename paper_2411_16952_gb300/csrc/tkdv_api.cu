@@ -177,6 +177,15 @@ const void *main_fn(const tkdv_sampler *h, int variant) {
     return h->kt.main[uni][variant];
 }
 
+// Dynamic shared memory of one CTA of the current form with `threads` threads:
+// the grid form's tiles, or the triad form's accept hand-off (none in SIR runs
+// and in the warp form).
+size_t main_dyn_smem(const tkdv_sampler *h, int threads) {
+    if (is_grid(h)) return h->dyn_smem;
+    if (h->opt.sir) return 0;
+    return (size_t)threads * (size_t)h->kt.xfer_bytes_per_thread;
+}
+
 // TMEM columns one grid-form CTA allocates.
 int grid_tmem_cols(const tkdv_sampler *h) {
     int c = 32;
@@ -187,8 +196,7 @@ int grid_tmem_cols(const tkdv_sampler *h) {
 // Largest number of resident CTAs per SM for the handle's form.
 int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads,
-                                                     is_grid(h) ? h->dyn_smem : 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads, main_dyn_smem(h, threads)));
     if (is_grid(h)) {
         // The grid kernel's residency follows from its own limits: shared
         // memory (with the per-block reservation), allocated registers, and
@@ -289,7 +297,7 @@ int build_graph(tkdv_sampler *h) {
     kp.func = (void *)main_fn(h, h->launch.variant);
     kp.gridDim = dim3(h->launch.ctas);
     kp.blockDim = dim3(h->launch.threads);
-    kp.sharedMemBytes = is_grid(h) ? (unsigned)h->dyn_smem : 0;
+    kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.threads);
     kp.kernelParams = margs;
     CK(cudaGraphAddKernelNode(&h->n_main, h->graph, &n_ms, 1, &kp));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -319,7 +327,7 @@ int enqueue(tkdv_sampler *h) {
         kp.func = (void *)main_fn(h, h->launch.variant);
         kp.gridDim = dim3(h->launch.ctas);
         kp.blockDim = dim3(h->launch.threads);
-        kp.sharedMemBytes = is_grid(h) ? (unsigned)h->dyn_smem : 0;
+        kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.threads);
         kp.kernelParams = margs;
         CK(cudaGraphExecKernelNodeSetParams(h->exec, h->n_main, &kp));
         void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -337,7 +345,7 @@ int enqueue(tkdv_sampler *h) {
     int gN = h->grid_N;
     void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
     CK(cudaLaunchKernel(main_fn(h, h->launch.variant), dim3(h->launch.ctas), dim3(h->launch.threads), margs,
-                        is_grid(h) ? h->dyn_smem : 0, h->stream));
+                        main_dyn_smem(h, h->launch.threads), h->stream));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
     CK(cudaLaunchKernel(h->kt.refine[uni], dim3(refine_grid(h)), dim3(128), rargs, 0, h->stream));
     return TKDV_OK;
@@ -466,6 +474,21 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if (e != cudaSuccess) {
         h->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
         return bail(TKDV_ERR_CUDA);
+    }
+    // the triad form's accept hand-off may exceed the 48 KB default
+    if (h->kt.xfer_bytes_per_thread > 0) {
+        for (int u = 0; u < 2 && e == cudaSuccess; ++u)
+            for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+                e = cudaFuncSetAttribute(h->kt.main[u][v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTriadVariantThreads[v] * h->kt.xfer_bytes_per_thread);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(h->kt.main[u][v], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+            }
+        if (e != cudaSuccess) {
+            h->err = std::string("triad kernel shared memory: ") + cudaGetErrorString(e);
+            return bail(TKDV_ERR_CUDA);
+        }
     }
     h->launch.threads = opt->threads_per_cta ? opt->threads_per_cta : 256;
     h->launch.variant = h->launch.threads == 128 ? 0 : 1;

@@ -121,6 +121,7 @@ struct TriadKernels {
     const void *refine[2];
     const void *replay[2];
     int replay_per_block;  // indices one replay CTA of 128 threads handles
+    int xfer_bytes_per_thread;  // dynamic shared memory of the rejection kernels per thread (0: none)
 };
 void triad_kernels_k4(TriadKernels *t);
 void triad_kernels_k8(TriadKernels *t);

@@ -117,7 +117,13 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
     const void *fn = kt.main[uni][kmax == 128 ? 2 : 1];  // warp form: two CTAs per SM
     int sms = 0, nb = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
+    // the triad form's accept hand-off: dynamic shared memory beyond the 48 KB default
+    const size_t dyn = (size_t)256 * kt.xfer_bytes_per_thread;
+    if (e == cudaSuccess && dyn)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess && dyn)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, dyn);
     if (e != cudaSuccess) return TKDV_ERR_CUDA;
     const int ctas = std::max(1, nb) * sms;
 
@@ -154,7 +160,7 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
     if (e != cudaSuccess) return TKDV_ERR_CUDA;
     if (n_proposals > 0) {
         void *margs[] = {&B, &A, &k0, &k1};
-        e = cudaLaunchKernel(fn, dim3(ctas), dim3(256), margs, 0, st);
+        e = cudaLaunchKernel(fn, dim3(ctas), dim3(256), margs, dyn, st);
         if (e == cudaSuccess) {
             void *rargs[] = {&B, &k0, &k1};
             e = cudaLaunchKernel(kt.refine[uni], dim3(sms * 4), dim3(128), rargs, 0, st);
