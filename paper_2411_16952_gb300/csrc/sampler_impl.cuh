@@ -507,7 +507,12 @@ __device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long lo
 template <int KMAX>
 __host__ __device__ constexpr int xfer_stride() { return 2 * KMAX + 4; }
 
-template <int KMAX, bool UNIF, int NT, int MINB, bool SIR = false>
+// XFER: accepted draws hand their state to the warp through shared memory
+// (dynamic, xfer_stride floats per thread); else each accepted draw's lane
+// tallies its spectrum and writes its record itself.  The first pays off
+// once a warp iteration often holds an accepted draw, the second can spill
+// less under a tight register budget; the autotune times both.
+template <int KMAX, bool UNIF, int NT, int MINB, bool SIR = false, bool XFER = true>
 __global__ void __launch_bounds__(NT, MINB)
     k_sample_triad(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1) {
     __shared__ uint32_t s_hist[kHistBins];
@@ -628,78 +633,112 @@ __global__ void __launch_bounds__(NT, MINB)
             const bool acc = !SIR && valid && !defer && f.d < 0.f;
             if (!SIR && valid && !defer && f.delta > 0.f) atomicAdd(&s_cnt[1], 1u);
 
-            const unsigned ma = __ballot_sync(0xffffffffu, acc);
-            if (ma) {
-                const int leader = __ffs(ma) - 1;
-                unsigned long long slot0 = 0;
-                if (lane == leader) {
-                    slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(ma));
-                    atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
-                }
-                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                unsigned char *rec = nullptr;
-                bool redo = false;
-                if (acc) {
-                    const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
-                    if (slot < B.ring_cap)
-                        rec = B.ring + slot * B.rec_bytes;
-                    else
-                        atomicAdd(&s_cnt[2], 1u);
-                    redo = dr.rrmax * f.inv > kOutputRr;
-                    if (redo) {
-                        // a radius of the series range: outputs from rho_acc
-                        emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
-                                                  s_spec, rec);
-                    } else {
-                        const float u0 = sc.u0s * dr.u0raw * f.inv;
-                        tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
-                        if (rec) write_header(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta);
+            if constexpr (XFER) {
+                const unsigned ma = __ballot_sync(0xffffffffu, acc);
+                if (ma) {
+                    const int leader = __ffs(ma) - 1;
+                    unsigned long long slot0 = 0;
+                    if (lane == leader) {
+                        slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(ma));
+                        atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
                     }
-                }
-                // Spectrum and projected state of the other accepted draws: each
-                // hands its (x | y) to its warp through shared memory (one
-                // straight run of vector stores), then the warp takes the draws
-                // one at a time, lane m mode m.  So the hot loop carries no
-                // unrolled per-mode tally or record stores (which, executed in a
-                // quarter of the iterations at 1 % acceptance, cost the loop its
-                // instruction cache), the atomics do not contend and the record
-                // writes are coalesced.
-                const bool coop = acc && !redo;
-                if (coop) {
-                    float *xo = s_xfer + (size_t)tid * xfer_stride<KMAX>();
-#pragma unroll
-                    for (int m = 0; m < KMAX; m += 4) {
-                        *reinterpret_cast<float4 *>(xo + m) = make_float4(dr.x[m], dr.x[m + 1], dr.x[m + 2], dr.x[m + 3]);
-                        *reinterpret_cast<float4 *>(xo + KMAX + m) =
-                            make_float4(dr.y[m], dr.y[m + 1], dr.y[m + 2], dr.y[m + 3]);
+                    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                    unsigned char *rec = nullptr;
+                    bool redo = false;
+                    if (acc) {
+                        const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
+                        if (slot < B.ring_cap)
+                            rec = B.ring + slot * B.rec_bytes;
+                        else
+                            atomicAdd(&s_cnt[2], 1u);
+                        redo = dr.rrmax * f.inv > kOutputRr;
+                        if (redo) {
+                            // a radius of the series range: outputs from rho_acc
+                            emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
+                                                      s_spec, rec);
+                        } else {
+                            const float u0 = sc.u0s * dr.u0raw * f.inv;
+                            tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
+                            if (rec) write_header(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta);
+                        }
                     }
-                }
-                unsigned mq = __ballot_sync(0xffffffffu, coop);
-                __syncwarp();
-                while (mq) {
-                    const int L = __ffs(mq) - 1;
-                    mq &= mq - 1;
-                    const float *xf = s_xfer + (size_t)((tid & ~31) + L) * xfer_stride<KMAX>();
-                    const float inv = __shfl_sync(0xffffffffu, f.inv, L);
-                    float *xh = reinterpret_cast<float *>(
-                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rec), L));
-                    const float sc2 = (inv * inv) * kSpecScale;
+                    // Spectrum and projected state of the other accepted draws: each
+                    // hands its (x | y) to its warp through shared memory (one
+                    // straight run of vector stores), then the warp takes the draws
+                    // one at a time, lane m mode m.  So the hot loop carries no
+                    // unrolled per-mode tally or record stores (which, executed in a
+                    // quarter of the iterations at 1 % acceptance, cost the loop its
+                    // instruction cache), the atomics do not contend and the record
+                    // writes are coalesced.
+                    const bool coop = acc && !redo;
+                    if (coop) {
+                        float *xo = s_xfer + (size_t)tid * xfer_stride<KMAX>();
 #pragma unroll
-                    for (int m0 = 0; m0 < KMAX; m0 += 32) {
-                        const int m = m0 + lane;
-                        if (m < sc.K) {
-                            const float x = xf[m], y = xf[KMAX + m];
-                            atomicAdd(&s_spec[m], (unsigned long long)__float2ull_rn(fmaf(x, x, y * y) * sc2));
-                            if (xh) {
-                                xh[8 + m] = x * inv;
-                                xh[8 + sc.K + m] = y * inv;
+                        for (int m = 0; m < KMAX; m += 4) {
+                            *reinterpret_cast<float4 *>(xo + m) = make_float4(dr.x[m], dr.x[m + 1], dr.x[m + 2], dr.x[m + 3]);
+                            *reinterpret_cast<float4 *>(xo + KMAX + m) =
+                                make_float4(dr.y[m], dr.y[m + 1], dr.y[m + 2], dr.y[m + 3]);
+                        }
+                    }
+                    unsigned mq = __ballot_sync(0xffffffffu, coop);
+                    __syncwarp();
+                    while (mq) {
+                        const int L = __ffs(mq) - 1;
+                        mq &= mq - 1;
+                        const float *xf = s_xfer + (size_t)((tid & ~31) + L) * xfer_stride<KMAX>();
+                        const float inv = __shfl_sync(0xffffffffu, f.inv, L);
+                        float *xh = reinterpret_cast<float *>(
+                            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rec), L));
+                        const float sc2 = (inv * inv) * kSpecScale;
+#pragma unroll
+                        for (int m0 = 0; m0 < KMAX; m0 += 32) {
+                            const int m = m0 + lane;
+                            if (m < sc.K) {
+                                const float x = xf[m], y = xf[KMAX + m];
+                                atomicAdd(&s_spec[m], (unsigned long long)__float2ull_rn(fmaf(x, x, y * y) * sc2));
+                                if (xh) {
+                                    xh[8 + m] = x * inv;
+                                    xh[8 + sc.K + m] = y * inv;
+                                }
                             }
                         }
                     }
+                    __syncwarp();  // the slabs are rewritten in the next iteration
                 }
-                __syncwarp();  // the slabs are rewritten in the next iteration
+            } else {
+                const unsigned ma = __ballot_sync(0xffffffffu, acc);
+                if (ma) {
+                    const int leader = __ffs(ma) - 1;
+                    unsigned long long slot0 = 0;
+                    if (lane == leader) {
+                        slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(ma));
+                        atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
+                    }
+                    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                    if (acc) {
+                        const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
+                        unsigned char *rec = nullptr;
+                        if (slot < B.ring_cap)
+                            rec = B.ring + slot * B.rec_bytes;
+                        else
+                            atomicAdd(&s_cnt[2], 1u);
+                        if (dr.rrmax * f.inv > kOutputRr) {
+                            // a radius of the series range: outputs from rho_acc
+                            emit_accepted<KMAX, UNIF>(P, idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
+                                                      s_spec, rec);
+                        } else {
+                            const float u0 = sc.u0s * dr.u0raw * f.inv;
+                            tally_accepted(u0, sc.ha, sc.hb, sc.ea, s_hist, s_exc, s_q);
+                            tally_spectrum<KMAX>(s_spec, dr.x, dr.y, f.inv * f.inv, sc.K);
+                            if (rec)
+                                write_record<KMAX>(rec, idx, (uint32_t)p, 0u, sc.E0 * f.S, sc.h3s * f.T, u0, f.delta,
+                                                   dr.x, dr.y, f.inv, sc.K);
+                        }
+                    }
+                }
             }
         }
+
         // chunk done: flush this CTA's partials into the point's StatBlock
         uint32_t key = fkey(maxd);
         key = __reduce_max_sync(0xffffffffu, key);
@@ -913,6 +952,14 @@ void fill_triad_kernels(TriadKernels *t) {
     t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128, 1>;
     t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256, 1>;
     t->main[1][2] = (const void *)k_sample_triad<KMAX, true, 256, 2>;
+    // the same launch shapes without the accept hand-off
+    t->main[0][3] = (const void *)k_sample_triad<KMAX, false, 128, 1, false, false>;
+    t->main[0][4] = (const void *)k_sample_triad<KMAX, false, 256, 1, false, false>;
+    t->main[0][5] = (const void *)k_sample_triad<KMAX, false, 256, 2, false, false>;
+    t->main[1][3] = (const void *)k_sample_triad<KMAX, true, 128, 1, false, false>;
+    t->main[1][4] = (const void *)k_sample_triad<KMAX, true, 256, 1, false, false>;
+    t->main[1][5] = (const void *)k_sample_triad<KMAX, true, 256, 2, false, false>;
+    t->n_variants = 6;
     t->sir[0] = (const void *)k_sample_triad<KMAX, false, 256, 1, true>;
     t->sir[1] = (const void *)k_sample_triad<KMAX, true, 256, 1, true>;
     t->refine[0] = (const void *)k_refine<KMAX, false>;

@@ -698,6 +698,7 @@ void triad_kernels_k128(TriadKernels *t) {
     t->replay[1] = (const void *)k_replay_warp<true>;
     t->replay_per_block = 32 * kReplayWarps / 32 * kWQ;
     t->xfer_bytes_per_thread = 0;
+    t->n_variants = 3;
 }
 
 }  // namespace tkdv

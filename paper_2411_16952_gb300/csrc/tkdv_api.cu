@@ -177,12 +177,12 @@ const void *main_fn(const tkdv_sampler *h, int variant) {
     return h->kt.main[uni][variant];
 }
 
-// Dynamic shared memory of one CTA of the current form with `threads` threads:
-// the grid form's tiles, or the triad form's accept hand-off (none in SIR runs
-// and in the warp form).
-size_t main_dyn_smem(const tkdv_sampler *h, int threads) {
+// Dynamic shared memory of one CTA of the current form in launch variant
+// `variant` with `threads` threads: the grid form's tiles, or the triad
+// form's accept hand-off (variants 0..2; none in SIR runs and in the warp form).
+size_t main_dyn_smem(const tkdv_sampler *h, int variant, int threads) {
     if (is_grid(h)) return h->dyn_smem;
-    if (h->opt.sir) return 0;
+    if (h->opt.sir || variant >= 3) return 0;
     return (size_t)threads * (size_t)h->kt.xfer_bytes_per_thread;
 }
 
@@ -196,7 +196,8 @@ int grid_tmem_cols(const tkdv_sampler *h) {
 // Largest number of resident CTAs per SM for the handle's form.
 int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads, main_dyn_smem(h, threads)));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, main_fn(h, variant), threads,
+                                                     main_dyn_smem(h, variant, threads)));
     if (is_grid(h)) {
         // The grid kernel's residency follows from its own limits: shared
         // memory (with the per-block reservation), allocated registers, and
@@ -297,7 +298,7 @@ int build_graph(tkdv_sampler *h) {
     kp.func = (void *)main_fn(h, h->launch.variant);
     kp.gridDim = dim3(h->launch.ctas);
     kp.blockDim = dim3(h->launch.threads);
-    kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.threads);
+    kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.variant, h->launch.threads);
     kp.kernelParams = margs;
     CK(cudaGraphAddKernelNode(&h->n_main, h->graph, &n_ms, 1, &kp));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -327,7 +328,7 @@ int enqueue(tkdv_sampler *h) {
         kp.func = (void *)main_fn(h, h->launch.variant);
         kp.gridDim = dim3(h->launch.ctas);
         kp.blockDim = dim3(h->launch.threads);
-        kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.threads);
+        kp.sharedMemBytes = (unsigned)main_dyn_smem(h, h->launch.variant, h->launch.threads);
         kp.kernelParams = margs;
         CK(cudaGraphExecKernelNodeSetParams(h->exec, h->n_main, &kp));
         void *rargs[] = {&h->dev, &h->key0, &h->key1};
@@ -345,7 +346,7 @@ int enqueue(tkdv_sampler *h) {
     int gN = h->grid_N;
     void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
     CK(cudaLaunchKernel(main_fn(h, h->launch.variant), dim3(h->launch.ctas), dim3(h->launch.threads), margs,
-                        main_dyn_smem(h, h->launch.threads), h->stream));
+                        main_dyn_smem(h, h->launch.variant, h->launch.threads), h->stream));
     void *rargs[] = {&h->dev, &h->key0, &h->key1};
     CK(cudaLaunchKernel(h->kt.refine[uni], dim3(refine_grid(h)), dim3(128), rargs, 0, h->stream));
     return TKDV_OK;
@@ -812,7 +813,8 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
             const int rcf = set_form(h, form);
             if (rcf) return rcf;
         }
-        std::vector<int> var_list = {0, 1, 2};
+        std::vector<int> var_list;
+        for (int v = 0; v < h->kt.n_variants; ++v) var_list.push_back(v);
         if (is_grid(h)) var_list = {0};
         if (h->opt.sir) var_list = {1};
         for (int var : var_list) {

@@ -115,13 +115,15 @@ struct RunArgs {
 // Kernel table of one KMAX instantiation of the triad sampler.
 struct TriadKernels {
     // [uniform][variant]: 0: 128 threads; 1: 256 threads; 2: 256 threads held
-    // to 128 registers (two CTAs per SM)
-    const void *main[2][3];
+    // to 128 registers (two CTAs per SM); 3..5: the same without the accept
+    // hand-off (one-thread form only)
+    const void *main[2][6];
+    int n_variants;  // variants present (6, or 3 for the warp form)
     const void *sir[2];  // SIR form of the sampler (256 threads), [uniform]
     const void *refine[2];
     const void *replay[2];
     int replay_per_block;  // indices one replay CTA of 128 threads handles
-    int xfer_bytes_per_thread;  // dynamic shared memory of the rejection kernels per thread (0: none)
+    int xfer_bytes_per_thread;  // dynamic shared memory per thread of variants 0..2 (0: none)
 };
 void triad_kernels_k4(TriadKernels *t);
 void triad_kernels_k8(TriadKernels *t);
@@ -145,7 +147,7 @@ void grid_kernels_k64(GridKernels *t);
 // layout of shared memory: bytes [0, N*KA*2) hi, [N*KA*2, 2*N*KA*2) lo.
 void build_grid_image(int K, int kmax, int ka, int N, unsigned char *out);
 
-constexpr int kTriadVariantThreads[3] = {128, 256, 256};
+constexpr int kTriadVariantThreads[6] = {128, 256, 256, 128, 256, 256};
 
 inline size_t record_bytes(int K) {
     size_t b = 32 + 8 * (size_t)K;
