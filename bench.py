@@ -313,7 +313,7 @@ def main():
         S = T.Sampler(K, points, h3_mode=mode, grid_N=gN if mode == T.H3_GRID_BF16X3 else 0,
                       sample_capacity=1 << 21, stream=stream, sir=fname.startswith("sir"))
         if not args.no_autotune:
-            S.autotune(1 << 22)
+            S.autotune(1 << 24)
         seed = 0
         for _ in range(args.warmup):
             S.run(n, seed)
@@ -423,7 +423,7 @@ def main():
                 for p, (b, r) in enumerate(kw["points"])]
         SK = T.Sampler(kw["K"], kpts, sample_capacity=1 << 20, stream=stream)
         if not args.no_autotune:
-            SK.autotune(1 << 22)
+            SK.autotune(1 << 24)
         for _ in range(args.warmup):
             SK.run(kw["n"], 3)
         SK.sync()

@@ -277,9 +277,10 @@ int sampler_replay(tkdv_sampler *h, int p, const uint64_t *idx, uint64_t n, uint
                    double *out);
 
 /* sampler_autotune: time the persistent launch on `calib_proposals` per point
-   for each candidate (CTAs per SM, threads per CTA, chunk size) and keep the
-   fastest for later runs.  Resets statistics afterwards.  *best_us receives
-   the best time (may be NULL). */
+   for each candidate (CTAs per SM, threads per CTA and register budget, the
+   triad form's two accept paths, and for TKDV_H3_AUTO both H3 forms; best of
+   four timed runs each) and keep the fastest for later runs.  Resets
+   statistics afterwards.  *best_us receives the best time (may be NULL). */
 int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us);
 
 /* sampler_h3_form: the H3 form the next run uses, TKDV_H3_TRIAD_F32 or

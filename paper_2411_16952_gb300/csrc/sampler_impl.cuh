@@ -960,8 +960,8 @@ void fill_triad_kernels(TriadKernels *t) {
     t->main[1][4] = (const void *)k_sample_triad<KMAX, true, 256, 1, false, false>;
     t->main[1][5] = (const void *)k_sample_triad<KMAX, true, 256, 2, false, false>;
     t->n_variants = 6;
-    t->sir[0] = (const void *)k_sample_triad<KMAX, false, 256, 1, true>;
-    t->sir[1] = (const void *)k_sample_triad<KMAX, true, 256, 1, true>;
+    t->sir[0] = (const void *)k_sample_triad<KMAX, false, 256, 1, true, false>;
+    t->sir[1] = (const void *)k_sample_triad<KMAX, true, 256, 1, true, false>;
     t->refine[0] = (const void *)k_refine<KMAX, false>;
     t->refine[1] = (const void *)k_refine<KMAX, true>;
     t->replay[0] = (const void *)k_replay<KMAX, false>;

@@ -827,7 +827,7 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
                 h->launch.variant = var;
                 h->launch.ctas = per * h->num_sms;
                 float ms_best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 5; ++rep) {  // the first warms up; best of four
                     CK(cudaEventRecord(e0, h->stream));
                     const int rc = run_ranges(h, i0.data(), c.data(), 0x5EEDull + rep);
                     if (rc) return rc;
