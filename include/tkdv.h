@@ -297,6 +297,16 @@ int sampler_h3_form(const tkdv_sampler *h);
 int sampler_batch_run(const tkdv_point *points, int n_points, const tkdv_options *opt, const uint64_t *budgets,
                       uint64_t seed, tkdv_stats *out);
 
+/* sampler_set_launch: pin the launch shape of later runs instead of the
+   default or autotuned one.  variant: triad form 0 = 128 threads, 1 = 256
+   threads, 2 = 256 threads held to 128 registers (two CTAs per SM), 3..5 the
+   same with the per-lane accept path (for K > 64: 0..2 of the warp form; SIR
+   runs: 1; grid form: 0).  ctas_per_sm: 1 .. the occupancy maximum of that
+   variant, 0 for the maximum.  Results do not depend on the launch shape.
+   Errors: INVALID_ARG (no such variant for the handle's form, ctas_per_sm
+   above the maximum), CUDA. */
+int sampler_set_launch(tkdv_sampler *h, int variant, int ctas_per_sm);
+
 /* sampler_launch_config: the launch shape of the next run. */
 int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint32_t *chunk);
 

@@ -38,7 +38,7 @@ EXPORTED = ["tkdv_record_bytes", "sampler_create", "sampler_create_ex", "sampler
             "sampler_replay", "sampler_autotune", "sampler_launch_config", "sampler_last_error",
             "sampler_destroy", "tkdv_alpha_star", "tkdv_log_M", "sampler_run_static",
             "sampler_set_trace", "tkdv_check_radius_error", "tkdv_check_radius_error_log",
-            "sampler_h3_form", "sampler_batch_run", "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
+            "sampler_h3_form", "sampler_batch_run", "sampler_set_launch", "tkdv_mlp_create", "tkdv_mlp_destroy", "tkdv_mlp_last_error",
             "tkdv_mlp_features", "tkdv_mlp_get_params", "tkdv_mlp_set_params", "tkdv_mlp_infer",
             "tkdv_mlp_set_data", "tkdv_mlp_set_data_records", "tkdv_mlp_rows", "tkdv_mlp_step"]
 MLP_NPARAM = 8640
@@ -122,6 +122,7 @@ def lib():
             L.sampler_autotune.argtypes = [vp, u64, dp]
             L.sampler_launch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_uint32)]
             L.sampler_h3_form.argtypes = [vp]
+            L.sampler_set_launch.argtypes = [vp, i, i]
             L.sampler_batch_run.argtypes = [C.POINTER(tkdv_point), i, C.POINTER(tkdv_options), u64p, u64,
                                             C.POINTER(tkdv_stats)]
             L.sampler_last_error.argtypes = [vp]
@@ -296,6 +297,11 @@ def sampler_autotune(h, calib_proposals):
     us = C.c_double()
     _check(lib().sampler_autotune(h, calib_proposals, C.byref(us)), h)
     return us.value
+
+
+def sampler_set_launch(h, variant, ctas_per_sm=0):
+    """Pin the launch shape of later runs (see include/tkdv.h)."""
+    _check(lib().sampler_set_launch(h, variant, ctas_per_sm), h)
 
 
 def sampler_h3_form(h):
@@ -590,6 +596,9 @@ class Sampler:
 
     def h3_form(self):
         return sampler_h3_form(self.h)
+
+    def set_launch(self, variant, ctas_per_sm=0):
+        sampler_set_launch(self.h, variant, ctas_per_sm)
 
     def close(self):
         if self.h:

@@ -859,6 +859,28 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
     return sampler_reset(h);
 }
 
+int sampler_set_launch(tkdv_sampler *h, int variant, int ctas_per_sm) {
+    if (!h || ctas_per_sm < 0) return TKDV_ERR_INVALID_ARG;
+    bool ok;
+    if (is_grid(h))
+        ok = variant == 0;
+    else if (h->opt.sir)
+        ok = variant == 1;
+    else
+        ok = variant >= 0 && variant < h->kt.n_variants;
+    if (!ok) return fail(h, TKDV_ERR_INVALID_ARG, "no such launch variant for this handle's form");
+    const int thr = is_grid(h) ? 128 : kTriadVariantThreads[variant];
+    int nb = 0;
+    const int rc = max_ctas_per_sm(h, variant, thr, &nb);
+    if (rc) return rc;
+    if (nb < 1) return fail(h, TKDV_ERR_CUDA, "sampler kernel does not fit on an SM");
+    if (ctas_per_sm > nb) return fail(h, TKDV_ERR_INVALID_ARG, "ctas_per_sm above the occupancy maximum");
+    h->launch.threads = thr;
+    h->launch.variant = variant;
+    h->launch.ctas = (ctas_per_sm ? ctas_per_sm : nb) * h->num_sms;
+    return TKDV_OK;
+}
+
 int sampler_h3_form(const tkdv_sampler *h) {
     if (!h) return TKDV_ERR_INVALID_ARG;
     return h->launch.form;

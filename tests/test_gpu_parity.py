@@ -380,3 +380,36 @@ def test_batch_run_equals_a_handle(T):
         assert int_view(out[p]) == int_view(ref[p]), p
     with pytest.raises(T.TkdvError):
         T.sampler_batch_run(pts, T.make_options(200), budgets, 5)
+
+
+def test_every_launch_variant_gives_the_same_results(T):
+    """Each pinned launch shape (the six triad-form variants, one and the
+    most CTAs per SM) gives the same statistics and the same records at an
+    acceptance where most warp iterations hold an accepted draw."""
+    K, E0, bp, r, n, seed = 16, 1.0, 20.0, 75.0, 1 << 20, 6
+    lm = envelope(K, E0, bp, r, O.PAPER) - 2.5  # log M lowered: about 12 % accepted
+    pts = [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=4, logM=lm)]
+    ref = None
+    for variant in range(6):
+        for per in (1, 0):
+            S = T.Sampler(K, pts, sample_capacity=1 << 18)
+            S.set_launch(variant, per)
+            S.run_ranges([3], [n], seed)
+            st = S.stats()[0]
+            rec = S.samples(1 << 18)
+            S.close()
+            o = np.argsort(rec["idx"])
+            view = (int_view(st), tuple(np.round(st["spectrum"][:K] * 2.0**28).astype(np.int64).tolist()))
+            if ref is None:
+                ref, rref = view, {k: v[o] for k, v in rec.items()}
+                assert st["n_accepted"] > 10000
+                continue
+            assert view == ref, (variant, per)
+            for key in ("idx", "H2", "H3", "u0", "xhat"):
+                assert np.array_equal(rec[key][o], rref[key]), (variant, per, key)
+    S = T.Sampler(K, pts, sample_capacity=16)
+    with pytest.raises(T.TkdvError):
+        S.set_launch(6, 0)
+    with pytest.raises(T.TkdvError):
+        S.set_launch(0, 64)
+    S.close()
