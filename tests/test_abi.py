@@ -112,3 +112,44 @@ def test_library_envelope_K128_closed_form(libtkdv, bp):
     pt = O.make_point(K, 1.0, bp, 0.0, O.PAPER)
     lm_l = T.tkdv_log_M(K, bp, 1.0, 0.0, np.array(pt.sigma2[:K]))
     assert abs(lm_l - logM_r0_paper(K, bp)) < 1e-9 * (1 + abs(lm_l))
+
+
+def test_header_compiles_as_c(tmp_path):
+    """include/tkdv.h is plain C: a C99 translation unit that calls the main
+    entry points compiles without warnings (gcc -std=c99 -Wall -Wextra -Werror)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no gcc")
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "tkdv.h"
+int run(void) {
+    tkdv_sampler *h = NULL;
+    tkdv_stats st;
+    tkdv_point pt = {0};
+    tkdv_options opt = {0};
+    uint64_t budget = 1u << 20, n = 0;
+    double alpha = 0.0, logM = 0.0;
+    if (sampler_create(32, 40.0, 1.0, 225.0, TKDV_PROPOSAL_PAPER, &h) != TKDV_OK) {
+        fprintf(stderr, "%s\n", sampler_last_error(NULL));
+        return 1;
+    }
+    sampler_run(h, 1u << 20, 0);
+    sampler_stats(h, &st, 1);
+    sampler_samples(h, NULL, 0, 0, &n);
+    sampler_destroy(h);
+    pt.beta_p = 40.0; pt.E0 = 1.0; pt.r = 225.0; pt.proposal = TKDV_PROPOSAL_PAPER;
+    opt.K = 32; opt.h3_mode = TKDV_H3_AUTO; opt.sample_capacity = 16;
+    sampler_batch_run(&pt, 1, &opt, &budget, 7, &st);
+    tkdv_alpha_star(32, 40.0, &alpha);
+    tkdv_log_M(32, 40.0, 1.0, 225.0, NULL, &logM);
+    return (int)(st.n_accepted > 0) + (int)(tkdv_record_bytes(32) > 0);
+}
+""")
+    res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-c",
+                          "-I", os.path.join(ROOT, "include"), str(src), "-o", str(tmp_path / "use.o")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
