@@ -72,7 +72,7 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
     "grid": (159488.0 / (8 * 4194304), "ncu --set full capture prof_grid25 (k_sample_grid<32,0,1>)"),
-    "triad": (137728.0 / (8 * 4194304), "ncu --set full capture prof_triad25 (k_sample_triad<32,0,256,1,0>)"),
+    "triad": (128256.0 / (8 * 4194304), "ncu --set full capture prof_triad26 (k_sample_triad<32,0,256,1,0,1>)"),
 }
 
 
