@@ -380,7 +380,7 @@ def main():
         bw = workloads.batch_k32()
         bpts = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]), T.PROPOSAL_PAPER,
                              point_id=rank * 64 + p) for p in range(64)]
-        # both forms: the batch's acceptances reach 0.5, where the grid form's
+        # both forms: the batch's acceptances reach 4 %, where the grid form's
         # per-accept redraw weighs more than on the headline workload
         bforms = {}
         for best_form in [f for f in ("triad_f32_paper", "grid_bf16x3_paper") if f in results]:
