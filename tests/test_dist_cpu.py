@@ -58,8 +58,11 @@ def _worker(rank, world, port, q):
     import paper_2411_16952_gb300 as T
     _, rec = O.run_accepted(pt, 7, 3, start, count, cap=1 << 16)
     allrec = D.gather_records(_encode(rec, K, 0), T.tkdv_record_bytes(K))
+    # a rank with no records contributes nothing
+    mine = _encode(rec, K, 0) if rank == 0 else np.zeros(0, dtype=np.uint8)
+    only0 = D.gather_records(mine, T.tkdv_record_bytes(K))
     if rank == 0:
-        q.put((merged, allrec))
+        q.put((merged, allrec, only0, _encode(rec, K, 0)))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -73,7 +76,7 @@ def test_two_ranks_merge_to_one_run():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    merged, allrec = q.get(timeout=300)
+    merged, allrec, only0, rank0 = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -99,6 +102,7 @@ def test_two_ranks_merge_to_one_run():
     assert np.all(np.diff(g["idx"][g["idx"] < D.shard_range(n, 1, 2)[0]].astype(np.int64)) > 0)
     o = np.argsort(rec["idx"])
     assert np.array_equal(g["xhat"][np.argsort(g["idx"])], rec["xhat"][o][:, :2 * K].astype(np.float32))
+    assert np.array_equal(only0, rank0)
 
 
 def test_shard_range_covers_exactly():
