@@ -944,21 +944,28 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
     }
 }
 
+// Kernel table of one KMAX, in two halves that separate translation units
+// can instantiate (the 64-mode kernels take long to compile): the launch
+// variants with the accept hand-off, the SIR form, the FP64 pass and replay;
+// and the variants with the per-lane accept path.
 template <int KMAX>
-void fill_triad_kernels(TriadKernels *t) {
-    t->main[0][0] = (const void *)k_sample_triad<KMAX, false, 128, 1>;
-    t->main[0][1] = (const void *)k_sample_triad<KMAX, false, 256, 1>;
-    t->main[0][2] = (const void *)k_sample_triad<KMAX, false, 256, 2>;
-    t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128, 1>;
-    t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256, 1>;
-    t->main[1][2] = (const void *)k_sample_triad<KMAX, true, 256, 2>;
-    // the same launch shapes without the accept hand-off
+void fill_triad_kernels_lane(TriadKernels *t) {
     t->main[0][3] = (const void *)k_sample_triad<KMAX, false, 128, 1, false, false>;
     t->main[0][4] = (const void *)k_sample_triad<KMAX, false, 256, 1, false, false>;
     t->main[0][5] = (const void *)k_sample_triad<KMAX, false, 256, 2, false, false>;
     t->main[1][3] = (const void *)k_sample_triad<KMAX, true, 128, 1, false, false>;
     t->main[1][4] = (const void *)k_sample_triad<KMAX, true, 256, 1, false, false>;
     t->main[1][5] = (const void *)k_sample_triad<KMAX, true, 256, 2, false, false>;
+}
+
+template <int KMAX>
+void fill_triad_kernels_xfer(TriadKernels *t) {
+    t->main[0][0] = (const void *)k_sample_triad<KMAX, false, 128, 1>;
+    t->main[0][1] = (const void *)k_sample_triad<KMAX, false, 256, 1>;
+    t->main[0][2] = (const void *)k_sample_triad<KMAX, false, 256, 2>;
+    t->main[1][0] = (const void *)k_sample_triad<KMAX, true, 128, 1>;
+    t->main[1][1] = (const void *)k_sample_triad<KMAX, true, 256, 1>;
+    t->main[1][2] = (const void *)k_sample_triad<KMAX, true, 256, 2>;
     t->n_variants = 6;
     t->sir[0] = (const void *)k_sample_triad<KMAX, false, 256, 1, true, false>;
     t->sir[1] = (const void *)k_sample_triad<KMAX, true, 256, 1, true, false>;
@@ -968,6 +975,12 @@ void fill_triad_kernels(TriadKernels *t) {
     t->replay[1] = (const void *)k_replay<KMAX, true>;
     t->replay_per_block = 128;
     t->xfer_bytes_per_thread = (int)(xfer_stride<KMAX>() * sizeof(float));
+}
+
+template <int KMAX>
+void fill_triad_kernels(TriadKernels *t) {
+    fill_triad_kernels_xfer<KMAX>(t);
+    fill_triad_kernels_lane<KMAX>(t);
 }
 
 }  // namespace tkdv

@@ -130,6 +130,7 @@ void triad_kernels_k8(TriadKernels *t);
 void triad_kernels_k16(TriadKernels *t);
 void triad_kernels_k32(TriadKernels *t);
 void triad_kernels_k64(TriadKernels *t);
+void triad_kernels_k64_lane(TriadKernels *t);  // variants 3..5 of the 64-mode table
 // 65..128 modes: one warp per batch of four proposals (sampler_k128.cu).
 void triad_kernels_k128(TriadKernels *t);
 
