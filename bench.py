@@ -71,7 +71,7 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (159488.0 / (8 * 4194304), "ncu --set full capture prof_grid25 (k_sample_grid<32,0,1>)"),
+    "grid": (167680.0 / (8 * 4194304), "ncu --set full capture prof_grid26 (k_sample_grid<32,0,1>)"),
     "triad": (128256.0 / (8 * 4194304), "ncu --set full capture prof_triad26 (k_sample_triad<32,0,256,1,0,1>)"),
 }
 

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : (KMAX <= 32 ? 3 : 1))
                 unsigned char *ga_lo = ga_hi + ATILE;
                 float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
                 uint32_t wmin = 0xFFFFFFFFu;
-    #pragma unroll 2
+    #pragma unroll 4
                 for (int cch = 0; cch < KMAX / 4; ++cch) {
                     float v[8];
     #pragma unroll
