@@ -76,6 +76,12 @@ TRAFFIC_PER_PROPOSAL = {
 }
 
 
+def alu_peak(n_sms, peaks):
+    """Thread instructions per second the SMs can issue: SMs x 128 lanes x
+    the maximum SM clock (T-ops/s)."""
+    return n_sms * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
 def tensor_flops_per_proposal(K: int, grid_N: int) -> int:
     """Three BF16 products of a 2K-padded-to-64 row with the 2K x N basis."""
     ka = (2 * K + 63) // 64 * 64
@@ -155,8 +161,7 @@ def cpu_baseline(wl, pts, seconds=15.0, sample_points=2):
     ops = []
     for bp, r, pid in pts[:sample_points]:
         pt = O.make_point(K, E0, bp, r, O.PAPER)
-        from paper_2411_16952_gb300 import tkdv_log_M
-        pt.logM = tkdv_log_M(K, bp, E0, r, np.array(pt.sigma2[:K]))
+        pt.logM = _oracle_envelope(K, bp, E0, r, pt)
         ops.append((pt, pid))
     t0 = time.perf_counter()
     O.run_stats(ops[0][0], 0, ops[0][1], 0, 1 << 18, cores)
@@ -175,6 +180,42 @@ def cpu_baseline(wl, pts, seconds=15.0, sample_points=2):
                       "%d threads" % (n, len(ops), K, cores)}
 
 
+def oracle_h_error(T, wl, pts, stream, n=1 << 14):
+    """Error of the grid form's H3 (BF16 hi/lo x3 contraction, FP32 cube-sum)
+    against the FP64 oracle on a replayed subset: the first and last points of
+    the workload (paper proposal), n traced proposals each.  Reports the
+    scale-aware relative error |dH| / (|H2| + |C3/C2 H3|) and the error of the
+    beta H term of log f/(Mg), |beta' C3/C2 dH3 / (E0 K^2)|."""
+    import math
+    import torch
+    import oracle as O
+    K, E0, gN = wl["K"], wl["E0"], wl["grid_N"]
+    h3s = 2 * math.pi * (E0 / (2 * math.pi)) ** 1.5
+    rel, bh = [], []
+    for bp, r, pid in (pts[0], pts[-1]):
+        pt = O.make_point(K, E0, bp, r, O.PAPER)
+        pt.logM = _oracle_envelope(K, bp, E0, r, pt)
+        S = T.Sampler(K, [T.make_point(bp, E0, r, T.PROPOSAL_PAPER, point_id=pid, logM=pt.logM)],
+                      h3_mode=T.H3_GRID_BF16X3, grid_N=gN, sample_capacity=1 << 10, stream=stream)
+        tr = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+        S.set_trace(tr, n)
+        S.run_ranges([0], [n], 11)
+        S.sync()
+        S.close()
+        tr = tr.cpu().numpy().reshape(n, 2).astype(np.float64)
+        keep = ~np.isnan(tr[:, 0])
+        o = O.replay(pt, 11, pid, np.arange(n, dtype=np.uint64)[keep])
+        dH3 = h3s * tr[keep, 1] - o["H3"]
+        rel.append(np.abs(r * dH3) / (np.abs(o["H2"]) + np.abs(r * o["H3"])))
+        bh.append(np.abs(bp * r / (E0 * K * K) * dH3))
+    rel, bh = np.concatenate(rel), np.concatenate(bh)
+    return {"h_rel_max": float(rel.max()), "h_rel_median": float(np.median(rel)),
+            "beta_h_abs_max": float(bh.max()), "beta_h_abs_median": float(np.median(bh)),
+            "tolerance": 1e-5, "proposals": int(rel.size),
+            "sample": "grid form (paper proposal), %d traced proposals of the first and last points, "
+                      "against the FP64 oracle's replay" % n}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, per step a bounded
     sample of the same workload (one point per step, cycling)."""
@@ -189,7 +230,7 @@ def run_reference(args):
     pts = []
     for p, (bp, r) in enumerate(wl["points"]):
         pt = O.make_point(K, E0, bp, r, O.PAPER)
-        pt.logM = O.log_M(pt, 0) if args.ref_exact_envelope else _lib_envelope(K, bp, E0, r, pt)
+        pt.logM = O.log_M(pt, 0) if args.ref_exact_envelope else _oracle_envelope(K, bp, E0, r, pt)
         pts.append((pt, p))
     n = args.ref_proposals
     for i in range(args.warmup):
@@ -220,9 +261,10 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def _lib_envelope(K, bp, E0, r, pt):
-    """The oracle needs log M; use its own Nelder-Mead (slow at K = 32) unless
-    a cached value is present in tests/golden/envelopes.json."""
+def _oracle_envelope(K, bp, E0, r, pt):
+    """The oracle's own log M (Nelder-Mead, Eq. 45): the cached value that
+    tests/golden/make_envelopes.py wrote with the oracle alone, or, for a
+    point not in that file, the oracle's search run here (slow at K = 32)."""
     import oracle as O
     path = os.path.join(ROOT, "tests", "golden", "envelopes.json")
     if os.path.exists(path):
@@ -267,6 +309,7 @@ def main():
     from paper_2411_16952_gb300 import _build
     _build.build()
     peaks, peak_src = measured_peaks()
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     wl, pts = workload_points(rank, args.n_per_point)
     K, E0, n, gN = wl["K"], wl["E0"], args.n_per_point, wl["grid_N"]
     stream = torch.cuda.Stream()
@@ -442,7 +485,7 @@ def main():
         kprop = sum(s["n_proposals"] for s in kst)
         kacc = sum(s["n_accepted"] for s in kst)
         kops = alg_ops_per_proposal(kw["K"], "triad")
-        kpeak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        kpeak = alu_peak(n_sms, peaks)
         kpps = kprop / (kms * args.steps / 1e3)
         k128 = {"workload": kw["name"], "K": kw["K"], "ms_per_step": kms, "proposals_per_s": kpps,
                 "accepted_per_s": kacc / (kms * args.steps / 1e3), "acceptance": kacc / kprop,
@@ -460,7 +503,7 @@ def main():
     step_s = h["ms_per_step"] / 1e3
     props_per_step = h["proposals_per_s"] * step_s
     achieved = ops * props_per_step / step_s / 1e12
-    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = alu_peak(n_sms, peaks)
     tr = TRAFFIC_PER_PROPOSAL.get(form_kind)
     traffic = None if tr is None or tr[0] is None else tr[0] * props_per_step
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
@@ -468,7 +511,7 @@ def main():
             "algorithmic_bytes_per_launch": h["acceptance"] * props_per_step * T.tkdv_record_bytes(K) + STAT_BYTES_PER_POINT * len(pts),
             "ops_per_proposal": ops, "kernel": "k_sample_%s" % form_kind,
             "note": "ideal thread-instruction count per proposal (bench.py alg_ops_per_proposal); peak = "
-                    "152 SM x 128 lanes x max SM clock (%s sm_max_mhz)" % peak_src}
+                    "%d SMs (device) x 128 lanes x max SM clock (%s sm_max_mhz)" % (n_sms, peak_src)}
     if form_kind == "grid":
         tf = tensor_flops_per_proposal(K, gN) * h["proposals_per_s"] / 1e12
         roof["tensor"] = {"achieved_tflops": tf, "peak_tflops": float(peaks.get("bf16_tflops_sustained", 1735.3)),
@@ -486,7 +529,9 @@ def main():
         if "triad_f32_paper" in results else None,
         "learned": learned_info, "batch_64pts": batch, "k128": k128,
         "config": {"workload": wl["name"], "K": K, "grid_N": gN, "points": len(pts),
-                   "proposals_per_point_per_step": n, "proposal": "paper",
+                   "proposals_per_point_per_step": n,
+                   "proposal": "learned" if headline.endswith("learned") else "paper",
+                   "h3_form": "grid_bf16x3" if form_kind == "grid" else "triad_f32",
                    "l2": "256 MiB buffer written between timed steps, outside the step events",
                    "parallelism": "points x index ranges, weak per GPU"},
         "roofline": roof,
@@ -497,7 +542,11 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the oracle leg: the FP64 oracle timed on the host cores, and the
+        # grid form's H error measured against it
         line["cpu_baseline"] = cpu_baseline(wl, pts, args.cpu_seconds)
+        if any(f.startswith("grid") for f in results):
+            line["h_error_vs_fp64"] = oracle_h_error(T, wl, pts, stream)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

@@ -259,7 +259,7 @@ int sampler_set_deadline_ns(tkdv_sampler *h, uint64_t ns);
    for each of point 0's first n proposals of the run (index idx0[0] + i),
    the pair (log f/(Mg), T) as two floats at dev_buf[2i], where
    H3 = 2 pi (E0/2pi)^{3/2} T (Eq. 42 in these units).  A proposal with a
-   refined word (about 2K+1 in 2^23, see the stream rule above) is decided in
+   refined word (K radius words and the accept word: about K+1 in 2^23, see the stream rule above) is decided in
    the FP64 pass only and traced as two NaNs.  dev_buf is the
    caller's device buffer of 2n floats; n = 0 switches the trace off.
    Errors: INVALID_ARG, UNSUPPORTED (triad form). */
@@ -332,8 +332,11 @@ int sampler_launch_config(tkdv_sampler *h, int *ctas, int *threads_per_cta, uint
                  logM (tkdv_log_M computes it), else TKDV_ERR_INVALID_ARG
      n_proposals at most TKDV_STATIC_MAX_PROPOSALS, else TKDV_ERR_TOO_LARGE
                  (split larger ranges over several calls with advancing idx0)
-     records     caller's DEVICE buffer of capacity records of
-                 tkdv_record_bytes(K) bytes (may be NULL with capacity 0)
+     records     caller's DEVICE buffer on the current device, holding at
+                 least capacity * tkdv_record_bytes(K) bytes (may be NULL
+                 with capacity 0); the kernels write up to capacity records
+                 into it, so a smaller buffer is overrun (the library cannot
+                 check the size of a raw pointer)
      n_records   host; records written (<= capacity), may be NULL
      stats       host; statistics of this call alone, may be NULL
      cuda_stream stream to run on (NULL: the legacy default stream)

@@ -343,10 +343,28 @@ def sampler_destroy(h):
 def sampler_run_static(K, point, idx0, n_proposals, seed, records=None, capacity=0, stream=None):
     """One run that allocates nothing (see include/tkdv.h): for callers whose
     device memory is owned elsewhere or who must not call cudaMalloc.
-    records: the caller's torch uint8 CUDA tensor of capacity records (or None).
-    Returns (stats dict, number of records written)."""
+    records: the caller's contiguous torch uint8 tensor on the current CUDA
+    device, holding at least capacity * tkdv_record_bytes(K) bytes (or None
+    with capacity 0); anything else raises TkdvError(INVALID_ARG) before the
+    library is called.  Returns (stats dict, number of records written)."""
     st = tkdv_stats()
     nrec = C.c_uint64()
+    if records is not None:
+        # the kernels write up to `capacity` records into this buffer: it must
+        # be a uint8 tensor on the current CUDA device holding them all
+        import torch
+        rb = tkdv_record_bytes(K)
+        if not (isinstance(records, torch.Tensor) and records.is_cuda and records.dtype == torch.uint8
+                and records.is_contiguous()):
+            raise TkdvError(-1, "sampler_run_static: records must be a contiguous uint8 CUDA tensor")
+        if records.device.index != torch.cuda.current_device():
+            raise TkdvError(-1, "sampler_run_static: records are on cuda:%d, the current device is cuda:%d"
+                            % (records.device.index, torch.cuda.current_device()))
+        if capacity < 0 or capacity * rb > records.numel():
+            raise TkdvError(-1, "sampler_run_static: %d records of %d bytes do not fit a buffer of %d bytes"
+                            % (capacity, rb, records.numel()))
+    elif capacity:
+        raise TkdvError(-1, "sampler_run_static: capacity > 0 needs a records buffer")
     dst = C.c_void_p(records.data_ptr()) if records is not None else None
     s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)) or 1)
     rc = lib().sampler_run_static(K, C.byref(point), idx0, n_proposals, seed, dst,

@@ -91,6 +91,11 @@ def test_two_ranks_merge_to_one_run():
     assert np.allclose(merged[0]["sum_u0"], one["sum_u0"], rtol=1e-12)
     assert np.allclose(merged[0]["spectrum"], one["spectrum"], rtol=1e-12, atol=1e-9)
     assert merged[0]["max_delta"] == one["max_delta"]
+    # moments recomputed from the merged sums; counters absent from the input stay zero
+    m = D.moments(one["n_accepted"], one["sum_u0"])
+    for k in ("mean", "var", "skew", "kurt"):
+        assert abs(merged[0][k] - m[k]) <= 1e-9 * (1 + abs(m[k])), k
+    assert merged[0]["n_kept"] == 0 and merged[0]["sir_sum_w"] == 0.0
     # rank-specific streams: point ids 1 and 3 are different draws
     assert merged[1]["n_proposals"] == 100_000
     # the gathered records are the one run's accepted draws, rank 0's first

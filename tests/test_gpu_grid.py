@@ -64,7 +64,7 @@ def test_grid_trace_matches_oracle(T, K, N, E0, bp, r):
     st = S.stats()[0]
     S.close()
     tr = tr.cpu().numpy().reshape(n, 2).astype(np.float64)
-    # draws with a word in the lowest bucket of the uniform map (about 2K + 1
+    # draws with a word in the lowest bucket of the uniform map (about K + 1
     # in 2^23) are traced as NaN: they are decided in FP64 with the refined tail
     keep = ~np.isnan(tr[:, 0])
     assert np.sum(~keep) <= 4
