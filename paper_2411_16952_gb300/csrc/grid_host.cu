@@ -1,8 +1,9 @@
 // grid_host.cu - host construction of the grid basis of the tensor-core form:
-// row j is grid point xi_j = -pi + 2 pi j / N (the rectangle rule of Eq. 2);
-// column 8c + 2e + s is mode k = 4c + e + 1 with cos(k xi_j) (s = 0) or
-// sin(k xi_j) (s = 1), zero for modes above K and for the padding columns;
-// every value is split into BF16 hi + lo.
+// row j is the mirror pair of grid points +-xi_j, xi_j = pi (2j + 1)/N,
+// j = 0..N/2-1 (the N-point rectangle rule of Eq. 2, offset by half a step);
+// column i of the cosine part (i < KA/2) holds cos(k xi_j) and column KA/2 + i
+// of the sine part sin(k xi_j), k = i + 1, zero for modes above K and for the
+// padding; every value is split into BF16 hi + lo.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -26,18 +27,18 @@ float bf16_to_f(uint16_t h) {
 }  // namespace
 
 void build_grid_image(int K, int kmax, int ka, int N, unsigned char *out) {
-    const size_t tile = (size_t)N * ka * 2;
+    const int half = N / 2, part = ka / 2;
+    const size_t tile = (size_t)half * ka * 2;
     std::memset(out, 0, 2 * tile);
-    for (int j = 0; j < N; ++j) {
-        const double xi = -M_PI + 2.0 * M_PI * (double)j / (double)N;
+    for (int j = 0; j < half; ++j) {
+        const double xi = M_PI * (double)(2 * j + 1) / (double)N;
         for (int i = 0; i < ka; ++i) {
+            const int sine = i >= part, k = (i % part) + 1;
             double v = 0.0;
-            const int c = i / 8, e = (i % 8) / 2, s = i % 2;
-            const int k = 4 * c + e + 1;
-            if (k <= K && k <= kmax) v = s ? std::sin(k * xi) : std::cos(k * xi);
+            if (k <= K && k <= kmax) v = sine ? std::sin(k * xi) : std::cos(k * xi);
             const uint16_t hi = bf16_rn((float)v);
             const uint16_t lo = bf16_rn((float)(v - (double)bf16_to_f(hi)));
-            const uint32_t off = sw128_offset((uint32_t)j, (uint32_t)i, (uint32_t)N);
+            const uint32_t off = sw128_offset((uint32_t)j, (uint32_t)i, (uint32_t)half);
             std::memcpy(out + off, &hi, 2);
             std::memcpy(out + tile + off, &lo, 2);
         }

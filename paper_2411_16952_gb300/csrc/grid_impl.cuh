@@ -1,29 +1,45 @@
 // grid_impl.cuh - the grid form of H3 on the 5th-generation tensor cores.
 //
-// Eq. (2) gives H3 = (1/6) int u^3; on the N-point grid xi_j = -pi + 2 pi j/N
-// with N > 3K the rectangle rule is exact, so for a tile of 128 proposals
-//   U = X B,   X: 128 x 2K (raw scaled normals, [cos | sin] halves),
-//              B: 2K x N  (B[k][j] = cos(k xi_j), B[K+k][j] = sin(k xi_j)),
-//   H3 = (pi/(3N)) sum_j (2 sqrt(E0/2pi) U_j / |x|)^3.
-// The contraction runs as three BF16 products with FP32 accumulation in
-// tensor memory: X = Xh + Xl, B = Bh + Bl, U ~ Xh Bh + Xh Bl + Xl Bh
-// (the dropped Xl Bl term is 2^-16 relative).
+// Eq. (2) gives H3 = (1/6) int u^3.  On N equispaced points the rectangle rule
+// integrates a trigonometric polynomial of degree below N exactly, whatever
+// the offset of the grid, and u^3 has degree 3K < N.  The grid here is
+// xi = +-xi_j, xi_j = pi (2j + 1)/N, j = 0..N/2-1 (the N-point grid offset by
+// half a step), so that its points come in mirror pairs.  With the cosine and
+// sine parts of the raw scaled normals,
+//   C_j = sum_k x_k cos(k xi_j),   S_j = sum_k y_k sin(k xi_j),
+// u(+-xi_j) is proportional to C_j +- S_j, and a pair contributes
+//   (C + S)^3 + (C - S)^3 = 2 C (C^2 + 3 S^2),
+// so that
+//   H3 = (pi/(3N)) sum_{all N points} u^3,  u = 2 sqrt(E0/2pi) U/|x|,
+// needs two contractions of K terms onto N/2 columns instead of one of 2K
+// terms onto N: half the multiply-adds of the plain grid contraction.
 //
-// CTA = one warpgroup of 128 threads; each tile has 128 rows (proposals):
-//   1. every thread makes its proposal (Philox, Box-Muller, sigma scaling as
-//      in the triad form) and writes its row of Xh and Xl (BF16) into a
-//      128B-swizzled K-major shared-memory tile.  The contraction index is
-//      ordered so that each 16-byte chunk holds (x_k, y_k) of four
-//      consecutive modes: column 8c + 2e + s is mode 4c + e + 1, cosine
-//      (s = 0) or sine (s = 1) half;
-//   2. after a CTA barrier one thread issues 3 * (KA/16) tcgen05.mma
-//      (M = 128, N = grid points, K = 16 each) into one of the CTA's TMEM
-//      accumulators and commits them to that accumulator's mbarrier;
+// On the tensor cores, for a tile of 128 proposals:
+//   C = Xc Bc,  S = Xs Bs,  Xc, Xs: 128 x K,  Bc, Bs: K x N/2,
+// each as three BF16 products with FP32 accumulation in tensor memory:
+// X = Xh + Xl, B = Bh + Bl, XB ~ Xh Bh + Xh Bl + Xl Bh (the dropped Xl Bl
+// term is 2^-16 relative).  The A tile holds a row per proposal in the
+// contraction order [cosine part | sine part], each part KA/2 columns (mode
+// k at column k - 1 of its part), BF16 in the 128-byte-swizzled K-major
+// layout; B holds the N/2 grid pairs as rows in the same column order.
+//
+// CTA = NWG warpgroups of 128 threads.  B (hi and lo) is loaded once per CTA
+// and shared; every warpgroup owns one A tile (hi and lo), one pair of TMEM
+// accumulators (C and S, N/2 columns each) and one mbarrier, and runs its own
+// persistent loop over chunks of proposal indices:
+//   1. each thread makes its proposal (Philox, Box-Muller, sigma scaling as in
+//      the triad form) and writes its row of Xh and Xl;
+//   2. after a warpgroup barrier one thread issues the 2 x 3 x K/16
+//      tcgen05.mma (M = 128, N = N/2, K = 16) and commits them to the
+//      warpgroup's mbarrier;
 //   3. every thread waits (bounded) on the mbarrier, reads its own TMEM lane
-//      with tcgen05.ld (32 columns at a time), and sums U_j^3;
-//   4. the decision, statistics and records are those of the triad form.
-// B (hi and lo) is built on the host once per handle, already in the
-// swizzled layout, and copied into shared memory when a CTA starts.
+//      (its proposal's C_j and S_j) and sums 2 C (C^2 + 3 S^2);
+//   4. the decision is that of the triad form; an accepted draw's index,
+//      T and log f/(Mg) go to its warp's slab in global memory, and at the
+//      end of the chunk the warp makes the outputs of its slab 32 draws at a
+//      time (the draw again with the accurate radius for the record's state,
+//      u(0) and spectrum), so that the hot loop never runs a divergent redraw.
+// While one warpgroup waits for its products, the others produce.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -39,6 +55,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Barrier of one warpgroup (named barrier 1 + g, 128 threads).
+__device__ __forceinline__ void wg_sync(int g) {
+    asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory");
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
@@ -90,21 +111,17 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -134,7 +151,9 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t
 
 template <int KMAX>
 struct GridShape {
-    static constexpr int KA = (2 * KMAX + 63) / 64 * 64;  // contraction length, whole swizzle atoms
+    static constexpr int KA = (2 * KMAX + 63) / 64 * 64;  // contraction columns: [cosine part | sine part]
+    static constexpr int PART = KA / 2;                   // columns of each part (mode k at column k - 1)
+    static constexpr int KSTEPS = (KMAX + 15) / 16;       // 16-column MMA steps per part
     static constexpr int A_TILE = 128 * KA * 2;           // bytes of one BF16 tile (hi or lo)
 };
 
@@ -153,106 +172,105 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// ---- the persistent grid-form sampler --------------------------------------
-// One warpgroup (128 threads) per CTA.  With NBUF = 2 the BF16 tiles and the
-// TMEM accumulators are double-buffered: after the MMAs of tile t are issued
-// the threads finish tile t-1 (wait, TMEM read, decision) and then make tile
-// t+1, so the tensor-core work of one tile overlaps the generation of the
-// next within the CTA.  With NBUF = 1 a CTA waits for its own MMAs and the
-// overlap comes from the other CTAs on the SM: for K <= 32 that layout holds
-// three CTAs per SM (168 registers, 512 TMEM columns / 128) where the
-// double-buffered one held two, and measured 24 % more proposals per second.
-// Dynamic shared memory: [B hi | B lo | NBUF x (A hi | A lo)], 1024-byte
-// aligned.
-struct GridPending {
-    unsigned long long idx;
-    float nrm2, Sraw, zz, esum;
-    bool valid;
-    bool tail;  // a radius word in the lowest bucket of the uniform map
+// Per-warpgroup shared state: the point being sampled and the statistics
+// partials of the current chunk (flushed to the point's StatBlock at its end).
+template <int KMAX>
+struct GridWG {
+    uint32_t hist[kHistBins];
+    uint32_t exc[kExcBins];
+    unsigned long long q[4];
+    unsigned long long spec[KMAX];
+    uint32_t cnt[4];  // accepted, envelope violations, dropped, fallbacks
+    uint32_t maxd;
+    uint32_t chunk;
+    uint32_t abort;
+    float sig[KMAX], act[KMAX];
 };
 
-template <int KMAX, bool UNIF, int NBUF>
-__global__ void __launch_bounds__(128, NBUF == 2 ? 2 : (KMAX <= 32 ? 3 : 1))
+// ---- the persistent grid-form sampler --------------------------------------
+// Dynamic shared memory (1024-byte aligned): [B hi | B lo | NWG x (A hi | A lo)].
+template <int KMAX, bool UNIF, int NWG>
+__global__ void __launch_bounds__(128 * NWG, 1)
     k_sample_grid(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1,
                   const unsigned char *__restrict__ bimg, int gridN) {
-    constexpr int NT = 128;
-    constexpr int KA = GridShape<KMAX>::KA;
-    constexpr int ATILE = GridShape<KMAX>::A_TILE;
+    using GS = GridShape<KMAX>;
+    constexpr int KA = GS::KA, PART = GS::PART, KSTEPS = GS::KSTEPS, ATILE = GS::A_TILE;
     extern __shared__ unsigned char dyn_smem[];
-    __shared__ uint32_t s_hist[kHistBins];
-    __shared__ uint32_t s_exc[kExcBins];
-    __shared__ unsigned long long s_q[4];
-    __shared__ unsigned long long s_spec[KMAX];
-    __shared__ uint32_t s_cnt[4];
-    __shared__ uint32_t s_maxd;
-    __shared__ uint32_t s_chunk;
-    __shared__ uint32_t s_abort;
+    __shared__ GridWG<KMAX> s_wg[NWG];
+    __shared__ __align__(8) unsigned long long s_mbar[NWG];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) unsigned long long s_mbar[NBUF];
-    __shared__ float s_sig[KMAX], s_act[KMAX];
+    __shared__ uint32_t s_abort;  // any warpgroup's device wait gave up: every warpgroup stops
 
-    const int tid = threadIdx.x, lane = tid & 31, row = tid;
-    const uint32_t btile = (uint32_t)gridN * KA * 2;  // bytes of one B tile
+    const int g = threadIdx.x >> 7, t = threadIdx.x & 127, lane = t & 31;
+    GridWG<KMAX> &W = s_wg[g];
+    const int half = gridN >> 1;                      // grid pairs = columns of C and of S
+    const uint32_t btile = (uint32_t)half * KA * 2;  // bytes of one B tile (hi or lo)
     const uint32_t base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
     unsigned char *gbase = dyn_smem + (base - smem_u32(dyn_smem));
     const uint32_t b_hi = base, b_lo = base + btile;
-    const uint32_t a0 = base + 2 * btile;  // A buffer b: hi at a0 + 2 b ATILE, lo at + ATILE
+    const uint32_t a_hi = base + 2 * btile + (uint32_t)g * 2u * ATILE, a_lo = a_hi + ATILE;
+    unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)g * 2u * ATILE;
+    unsigned char *ga_lo = ga_hi + ATILE;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(bimg);
         uint4 *dst = reinterpret_cast<uint4 *>(gbase);
-        for (uint32_t i = tid; i < 2 * btile / 16; i += NT) dst[i] = __ldg(src + i);
-        uint4 *az = reinterpret_cast<uint4 *>(gbase + 2 * btile);
-        for (uint32_t i = tid; i < (uint32_t)NBUF * 2 * ATILE / 16; i += NT) az[i] = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = threadIdx.x; i < 2 * btile / 16; i += 128 * NWG) dst[i] = __ldg(src + i);
     }
-    for (int e = tid; e < kHistBins; e += NT) s_hist[e] = 0;
-    for (int e = tid; e < KMAX; e += NT) s_spec[e] = 0ull;
-    if (tid < kExcBins) s_exc[tid] = 0;
-    if (tid < 4) {
-        s_q[tid] = 0ull;
-        s_cnt[tid] = 0;
+    for (int e = t; e < kHistBins; e += 128) W.hist[e] = 0;
+    for (int e = t; e < KMAX; e += 128) W.spec[e] = 0ull;
+    if (t < kExcBins) W.exc[t] = 0;
+    if (t < 4) {
+        W.q[t] = 0ull;
+        W.cnt[t] = 0;
     }
-    if (tid == 0) {
-        s_maxd = 0;
+    if (t == 0) {
+        W.maxd = 0;
+        W.abort = 0;
+    }
+    if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int b = 0; b < NBUF; ++b) mbar_init(smem_u32(&s_mbar[b]), 1);
+        for (int w = 0; w < NWG; ++w) mbar_init(smem_u32(&s_mbar[w]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // TMEM: per warpgroup C (N/2 columns) and S (N/2 columns)
     uint32_t tcols = 32;
-    while (tcols < (uint32_t)gridN) tcols <<= 1;
-    if (tid < 32) {
-        tmem_alloc(smem_u32(&s_tmem), tcols * NBUF);
+    while (tcols < (uint32_t)(NWG * gridN)) tcols <<= 1;
+    if (threadIdx.x < 32) {
+        tmem_alloc(smem_u32(&s_tmem), tcols);
         tmem_relinquish();
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem0 = s_tmem;
-    const uint32_t lane_off = ((uint32_t)(tid >> 5) * 32u) << 16;
-    const uint32_t idesc = idesc_bf16_f32(128, gridN);
-    uint32_t phase[NBUF];
-#pragma unroll
-    for (int b = 0; b < NBUF; ++b) phase[b] = 0;
-    bool waits_pending[NBUF];
-#pragma unroll
-    for (int b = 0; b < NBUF; ++b) waits_pending[b] = false;
-    const float tscale = 4.f / (3.f * (float)gridN);  // T = (4/(3N)) sum U^3 / |x|^3
+    const uint32_t tmem_c = s_tmem + (uint32_t)(g * gridN);
+    const uint32_t tmem_s = tmem_c + (uint32_t)half;
+    const uint32_t lane_off = ((uint32_t)(t >> 5) * 32u) << 16;
+    const uint32_t idesc = idesc_bf16_f32(128, half);
+    const uint32_t mbar = smem_u32(&s_mbar[g]);
+    uint32_t phase = 0;
+    bool pending = false;  // an MMA commit of this warpgroup not yet waited for
+    // this warp's slab: room for the accepted draws of one chunk (at most
+    // chunk / 4 proposals per warp)
+    AcceptItem *slab = B.accs + ((size_t)(blockIdx.x * NWG + g) * 4 + (size_t)(t >> 5)) * B.acc_slab;
+    const float tscale = 8.f / (3.f * (float)gridN);  // T = (4/(3N)) sum U^3/|x|^3, sum U^3 = 2 sum C (C^2 + 3 S^2)
+    const f32x2_t three = pk2(3.f, 3.f);
 
     const uint32_t total = A.chunk_prefix[A.n_points];
     const unsigned long long t0 = A.deadline_ns ? globaltimer_ns() : 0ull;
     for (;;) {
-        if (tid == 0) {
+        if (t == 0) {
             uint32_t c = atomicAdd(&B.counters[0], 1u);
             if (A.deadline_ns && c < total && globaltimer_ns() - t0 > A.deadline_ns) {
                 atomicOr(B.status, kStatusDeadline);
                 c = total;
             }
-            if (s_abort) c = total;
-            s_chunk = c;
+            if (*(volatile uint32_t *)&s_abort) c = total;
+            W.chunk = c;
         }
-        __syncthreads();
-        const uint32_t c = s_chunk;
+        wg_sync(g);
+        const uint32_t c = W.chunk;
         if (c >= total) break;
         int p = 0;
         while (p + 1 < A.n_points && A.chunk_prefix[p + 1] <= c) ++p;
@@ -261,69 +279,156 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : (KMAX <= 32 ? 3 : 1))
         const uint32_t n_here = left < A.chunk ? (uint32_t)left : A.chunk;
         const unsigned long long cbase = A.idx0[p] + local;
         const PointConst *P = B.pts + p;
-        if (tid < KMAX) {
-            s_sig[tid] = __ldg(&P->sigma[tid]);
-            s_act[tid] = __ldg(&P->act[tid]);
+        if (t < KMAX) {
+            W.sig[t] = __ldg(&P->sigma[t]);
+            W.act[t] = __ldg(&P->act[t]);
         }
         const Scal sc = load_scal(P);
-        __syncthreads();
+        wg_sync(g);
         float maxd = -INFINITY;
+        uint32_t nacc = 0;  // accepted draws of this warp in this chunk (the same in every lane)
 
-        // Finish one tile: wait for its MMAs, read U from TMEM, decide.
-        auto consume = [&](const GridPending &g, int b) {
-            float cube = 0.f;
-            bool ok = false;
-            if (waits_pending[b]) {
-                ok = mbar_wait_bounded(smem_u32(&s_mbar[b]), phase[b]);
-                if (ok) {
-                    phase[b] ^= 1u;
-                    waits_pending[b] = false;
-                    tc_fence_after();
-                    const uint32_t taddr = tmem0 + (uint32_t)b * tcols + lane_off;
-                    // sum of U^3 in four packed accumulators (columns e mod 8),
-                    // so that no single chain of dependent FMAs is long
-                    f32x2_t cq[4] = {0ull, 0ull, 0ull, 0ull};
-                    for (int cb = 0; cb < gridN; cb += 32) {
-                        float u[32];
-                        tmem_ld32(taddr + (uint32_t)cb, u);
-                        tmem_wait_ld();
+        for (uint32_t i0 = 0; i0 < n_here; i0 += 128) {
+            const uint32_t i = i0 + (uint32_t)t;
+            const bool valid = i < n_here;
+            const unsigned long long idx = cbase + i;
+            const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
+            // ---- 1. the row of X: eight modes (four Philox blocks) at a time,
+            // cosine values to part 0 and sine values to part 1 of the row
+            float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
+            uint32_t wmin = 0xFFFFFFFFu;
+#pragma unroll(NWG >= 4 ? 1 : 2)
+            for (int c8 = 0; c8 < KMAX / 8; ++c8) {
+                float vx[8], vy[8];
 #pragma unroll
-                        for (int e = 0; e < 32; e += 2) {
-                            const f32x2_t uu = pk2(u[e], u[e + 1]);
-                            cq[(e >> 1) & 3] = fma2(mul2(uu, uu), uu, cq[(e >> 1) & 3]);
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int j = 4 * c8 + jj;
+                    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk.k);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int m = 2 * j + h;
+                        const float s = UNIF ? W.act[m] : W.sig[m];
+                        float rho, xm, ym, rr;
+                        box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                        wmin = min(wmin, h ? w.z : w.x);
+                        esum = fmaf(s, rr, esum);
+                        vx[2 * jj + h] = xm;
+                        vy[2 * jj + h] = ym;
+                        const float sk = (s * s) * rho;
+                        nrm2 += sk;
+                        Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
+                        zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
+                    }
+                }
+                uint4 hx, lx, hy, ly;
+                split8(vx, hx, lx);
+                split8(vy, hy, ly);
+                const uint32_t ox = sw128_offset((uint32_t)t, (uint32_t)(8 * c8), 128u);
+                const uint32_t oy = sw128_offset((uint32_t)t, (uint32_t)(PART + 8 * c8), 128u);
+                *reinterpret_cast<uint4 *>(ga_hi + ox) = hx;
+                *reinterpret_cast<uint4 *>(ga_lo + ox) = lx;
+                *reinterpret_cast<uint4 *>(ga_hi + oy) = hy;
+                *reinterpret_cast<uint4 *>(ga_lo + oy) = ly;
+            }
+            const bool tail_r = wmin < kTailBucket;
+            fence_async_smem();
+            wg_sync(g);
+            // ---- 2. one thread issues the contraction of the tile
+            const bool run_mma = W.abort == 0;
+            if (run_mma) {
+                if (t == 0) {
+                    tc_fence_after();
+#pragma unroll
+                    for (int part = 0; part < 2; ++part) {
+                        const uint32_t dt = part ? tmem_s : tmem_c;
+#pragma unroll
+                        for (int ks = 0; ks < KSTEPS; ++ks) {
+                            const uint32_t kcol = (uint32_t)(part * PART + 16 * ks);
+                            const uint32_t koff = (kcol & 63u) * 2u;  // bytes into the swizzle atom
+                            const uint32_t aat = (kcol >> 6) * 128u * 128u;
+                            const uint32_t bat = (kcol >> 6) * (uint32_t)half * 128u;
+                            const uint64_t dah = sw128_desc(a_hi + aat + koff), dal = sw128_desc(a_lo + aat + koff);
+                            const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
+                            umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                            umma_bf16(dt, dah, dbl, idesc, 1u);
+                            umma_bf16(dt, dal, dbh, idesc, 1u);
                         }
                     }
-                    float c[8];
+                    umma_commit(mbar);
+                }
+                pending = true;
+            }
+            // ---- 3. wait for the products, sum 2 C (C^2 + 3 S^2) of this row
+            float cube = 0.f;
+            bool ok = false;
+            if (pending && !W.abort) {  // after a timeout of this warpgroup no thread waits again
+                ok = mbar_wait_bounded(mbar, phase);
+                if (ok) {
+                    phase ^= 1u;
+                    pending = false;
+                    tc_fence_after();
+                    // 32 columns of C and of S per wait where registers allow
+                    // (fewer round trips), then 16 at a time
+                    f32x2_t acc[2] = {0ull, 0ull};
+                    auto cube_sum = [&](const float *cv, const float *sv, int n) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) upk2(cq[q], c[2 * q], c[2 * q + 1]);
-                    cube = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+                        for (int e = 0; e < n; e += 2) {
+                            const f32x2_t C2 = pk2(cv[e], cv[e + 1]), S2 = pk2(sv[e], sv[e + 1]);
+                            const f32x2_t q = fma2(three, mul2(S2, S2), mul2(C2, C2));
+                            acc[(e >> 1) & 1] = fma2(C2, q, acc[(e >> 1) & 1]);
+                        }
+                    };
+                    int cb = 0;
+                    if (NWG <= 3) {
+                        for (; cb + 32 <= half; cb += 32) {
+                            float cv[32], sv[32];
+                            tmem_ld16(tmem_c + lane_off + (uint32_t)cb, cv);
+                            tmem_ld16(tmem_c + lane_off + (uint32_t)(cb + 16), cv + 16);
+                            tmem_ld16(tmem_s + lane_off + (uint32_t)cb, sv);
+                            tmem_ld16(tmem_s + lane_off + (uint32_t)(cb + 16), sv + 16);
+                            tmem_wait_ld();
+                            cube_sum(cv, sv, 32);
+                        }
+                    }
+                    for (; cb < half; cb += 16) {
+                        float cv[16], sv[16];
+                        tmem_ld16(tmem_c + lane_off + (uint32_t)cb, cv);
+                        tmem_ld16(tmem_s + lane_off + (uint32_t)cb, sv);
+                        tmem_wait_ld();
+                        cube_sum(cv, sv, 16);
+                    }
+                    float a0, a1, b0, b1;
+                    upk2(acc[0], a0, a1);
+                    upk2(acc[1], b0, b1);
+                    cube = (a0 + a1) + (b0 + b1);
                     tc_fence_before();
                 } else {
                     atomicOr(B.status, kStatusMbarTimeout);
+                    W.abort = 1;
                     s_abort = 1;
                 }
             }
-            const bool usable = g.valid && ok;
-            const uint32_t lo = (uint32_t)g.idx, hi = (uint32_t)(g.idx >> 32);
-            const float inv2 = 1.f / g.nrm2;
-            const float inv = rsqrtf(g.nrm2);
-            const float S = g.Sraw * inv2;
+            // ---- 4. decision
+            const bool usable = valid && ok;
+            const float inv2 = 1.f / nrm2;
+            const float inv = rsqrtf(nrm2);
+            const float S = Sraw * inv2;
             const float T = cube * tscale * (inv2 * inv);
             const float tS = sc.cS * S;
             const float tH = sc.cH * T;
-            const float tQ = UNIF ? 0.f : sc.cQ * logf(g.zz * inv2);
+            const float tQ = UNIF ? 0.f : sc.cQ * logf(zz * inv2);
             const float delta = ((tS + tH) + tQ) - sc.logM;
-            const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
+            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
             const float lnU = -0.5f * rho_fast(wa);
             const float d = lnU - delta;
             const float guard = fmaf(
-                sc.ge * g.esum, inv,
+                sc.ge * esum, inv,
                 fmaf(sc.gq, inv2, sc.ga + sc.gr * (fabsf(tS) + fabsf(tQ) + fabsf(tH) + fabsf(lnU) + fabsf(sc.logM)) + sc.gh));
             // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
-            const bool tail = g.tail || wa < kTailBucket;
+            const bool tail = tail_r || wa < kTailBucket;
             bool defer = usable && (fabsf(d) < guard || tail);
             if (usable && !tail) maxd = fmaxf(maxd, delta);
-            const unsigned long long li = g.idx - A.idx0[p];
+            const unsigned long long li = idx - A.idx0[p];
             if (A.trace && p == 0 && usable && li < A.trace_n) {
                 // a draw with a refined tail word is decided in FP64 only: NaN here
                 A.trace[2 * li] = tail ? __int_as_float(0x7fc00000) : delta;
@@ -339,189 +444,131 @@ __global__ void __launch_bounds__(128, NBUF == 2 ? 2 : (KMAX <= 32 ? 3 : 1))
                     const uint32_t slot = slot0 + __popc(md & ((1u << lane) - 1u));
                     if (slot < B.refine_cap) {
                         RefineItem it;
-                        it.idx = g.idx;
+                        it.idx = idx;
                         it.point = (uint32_t)p;
                         it.pad = 0;
                         B.refine[slot] = it;
                     } else {
                         atomicOr(B.status, kStatusRefineOverflow);
-                        atomicAdd(&s_cnt[3], 1u);
+                        atomicAdd(&W.cnt[3], 1u);
                         defer = false;
                     }
                 }
             }
             const bool acc = usable && !defer && d < 0.f;
-            if (usable && !defer && delta > 0.f) atomicAdd(&s_cnt[1], 1u);
+            if (usable && !defer && delta > 0.f) atomicAdd(&W.cnt[1], 1u);
+            // accepted draws: (index, T, log f/(Mg)) to this warp's slab
             const unsigned ma = __ballot_sync(0xffffffffu, acc);
             if (ma) {
-                const int leader = __ffs(ma) - 1;
-                unsigned long long slot0 = 0;
-                if (lane == leader) {
-                    slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(ma));
-                    atomicAdd(&s_cnt[0], (uint32_t)__popc(ma));
-                }
-                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
                 if (acc) {
-                    const unsigned long long slot = slot0 + __popc(ma & ((1u << lane) - 1u));
-                    unsigned char *rec = nullptr;
-                    if (slot < B.ring_cap)
-                        rec = B.ring + slot * B.rec_bytes;
-                    else
-                        atomicAdd(&s_cnt[2], 1u);
-                    // the grid form keeps no projected state: emit_accepted draws it again
-                    emit_accepted<KMAX, UNIF>(P, g.idx, (uint32_t)p, k0, k1, s_sig, s_act, s_hist, s_exc, s_q,
-                                              s_spec, rec);
+                    AcceptItem it;
+                    it.idx = idx;
+                    it.T = T;
+                    it.delta = delta;
+                    slab[nacc + __popc(ma & ((1u << lane) - 1u))] = it;
                 }
-            }
-        };
-
-        GridPending prev;
-        prev.valid = false;
-        prev.tail = false;
-        bool have_prev = false;
-        int b = 0;
-        // one extra trip with NBUF = 2 finishes the last tile (a single call
-        // site of consume keeps the code, and its instruction-cache footprint, small)
-        const uint32_t n_trips = (n_here + NT - 1) / NT + (NBUF == 2 ? 1u : 0u);
-        for (uint32_t trip = 0; trip < n_trips; ++trip) {
-            const bool produce = trip * NT < n_here;
-            const uint32_t i0 = trip * NT;
-            const uint32_t i = i0 + (uint32_t)tid;
-            GridPending cur;
-            cur.valid = produce && i < n_here;
-            cur.tail = false;
-            cur.idx = cbase + i;
-            if (produce) {
-                const uint32_t lo = (uint32_t)cur.idx, hi = (uint32_t)(cur.idx >> 32);
-                // Row of X in the contraction order: 16-byte chunk c holds
-                // (x, y) of modes 4c+1..4c+4, interleaved; chunk c is made from
-                // Philox blocks 2c and 2c+1 and stored at once (hi and lo).
-                unsigned char *ga_hi = gbase + 2 * btile + (uint32_t)b * 2u * ATILE;
-                unsigned char *ga_lo = ga_hi + ATILE;
-                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
-                uint32_t wmin = 0xFFFFFFFFu;
-    #pragma unroll 4
-                for (int cch = 0; cch < KMAX / 4; ++cch) {
-                    float v[8];
-    #pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        const int j = 2 * cch + jj;
-                        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, sc.pid), k0, k1);
-    #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int m = 2 * j + h;
-                            const float s = UNIF ? s_act[m] : s_sig[m];
-                            float rho, xm, ym, rr;
-                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
-                            wmin = min(wmin, h ? w.z : w.x);
-                            esum = fmaf(s, rr, esum);
-                            v[4 * jj + 2 * h] = xm;
-                            v[4 * jj + 2 * h + 1] = ym;
-                            const float sk = (s * s) * rho;
-                            nrm2 += sk;
-                            Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
-                            zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
-                        }
-                    }
-                    uint4 hv, lv;
-                    split8(v, hv, lv);
-                    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)cch * 8u, 128u);
-                    *reinterpret_cast<uint4 *>(ga_hi + off) = hv;
-                    *reinterpret_cast<uint4 *>(ga_lo + off) = lv;
-                }
-                cur.nrm2 = nrm2;
-                cur.Sraw = Sraw;
-                cur.zz = zz;
-                cur.esum = esum;
-                cur.tail = wmin < kTailBucket;
-                fence_async_smem();
-                __syncthreads();
-                if (!s_abort) {
-                    if (tid == 0) {
-                        tc_fence_after();
-                        const uint32_t ah = a0 + (uint32_t)b * 2u * ATILE, al = ah + ATILE;
-                        const uint32_t dt = tmem0 + (uint32_t)b * tcols;
-    #pragma unroll
-                        for (int ks = 0; ks < KA / 16; ++ks) {
-                            const uint32_t koff = (uint32_t)((ks & 3) * 32);  // 16 BF16 = 32 bytes per step
-                            const uint32_t aat = (uint32_t)(ks >> 2) * 128u * 128u;
-                            const uint32_t bat = (uint32_t)(ks >> 2) * (uint32_t)gridN * 128u;
-                            const uint64_t dah = sw128_desc(ah + aat + koff), dal = sw128_desc(al + aat + koff);
-                            const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
-                            umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                            umma_bf16(dt, dah, dbl, idesc, 1u);
-                            umma_bf16(dt, dal, dbh, idesc, 1u);
-                        }
-                        umma_commit(smem_u32(&s_mbar[b]));
-                    }
-                    waits_pending[b] = true;
-                }
-            }
-            if (NBUF == 2) {
-                if (have_prev) consume(prev, b ^ 1);
-                prev = cur;
-                have_prev = produce;
-                b ^= 1;
-            } else {
-                consume(cur, b);
+                nacc += (uint32_t)__popc(ma);
             }
         }
 
+        // ---- outputs of this warp's accepted draws of the chunk, 32 at a time:
+        // the draw again with the accurate radius (rho_acc) for the state,
+        // u(0), H2 and the spectrum; H3 from the grid contraction
+        __syncwarp();  // the slab entries other lanes wrote
+        if (lane == 0 && nacc) atomicAdd(&W.cnt[0], nacc);
+        for (uint32_t b0 = 0; b0 < nacc; b0 += 32) {
+            const bool has = b0 + (uint32_t)lane < nacc;
+            const unsigned mh = __ballot_sync(0xffffffffu, has);
+            unsigned long long slot0 = 0;
+            if (lane == 0) slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(mh));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (has) {
+                const AcceptItem it = slab[b0 + lane];
+                Draw<KMAX> dr;
+                draw_fast<KMAX, UNIF, true>(dr, W.sig, W.act, (uint32_t)it.idx, (uint32_t)(it.idx >> 32), sc.pid, k0,
+                                            k1);
+                const float inv2 = 1.f / dr.nrm2;
+                const float inv = rsqrtf(dr.nrm2);
+                const float u0 = sc.u0s * dr.u0raw * inv;
+                atomicAdd(&W.hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
+                atomicAdd(&W.exc[exc_bin(u0, sc.ea)], 1u);
+                const float u2 = u0 * u0;
+                atomicAdd(&W.q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
+                atomicAdd(&W.q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
+                atomicAdd(&W.q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
+                atomicAdd(&W.q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+                tally_spectrum<KMAX>(W.spec, dr.x, dr.y, inv2, sc.K);
+                const unsigned long long slot = slot0 + __popc(mh & ((1u << lane) - 1u));
+                if (slot < B.ring_cap)
+                    write_record<KMAX>(B.ring + slot * B.rec_bytes, it.idx, (uint32_t)p, 0u, sc.E0 * (dr.Sraw * inv2),
+                                       sc.h3s * it.T, u0, it.delta, dr.x, dr.y, inv, sc.K);
+                else
+                    atomicAdd(&W.cnt[2], 1u);
+            }
+        }
+
+        // chunk done: flush this warpgroup's partials into the point's StatBlock
         uint32_t key = fkey(maxd);
         key = __reduce_max_sync(0xffffffffu, key);
-        if (lane == 0 && maxd > -INFINITY) atomicMax(&s_maxd, key);
-        __syncthreads();
+        if (lane == 0 && maxd > -INFINITY) atomicMax(&W.maxd, key);
+        wg_sync(g);
         StatBlock *st = B.stats + p;
-        for (int e = tid; e < kHistBins; e += NT) {
-            if (s_hist[e]) {
-                atomicAdd(&st->hist[e], (unsigned long long)s_hist[e]);
-                s_hist[e] = 0;
+        for (int e = t; e < kHistBins; e += 128) {
+            if (W.hist[e]) {
+                atomicAdd(&st->hist[e], (unsigned long long)W.hist[e]);
+                W.hist[e] = 0;
             }
         }
-        if (tid < kExcBins && s_exc[tid]) {
-            atomicAdd(&st->exc[tid], (unsigned long long)s_exc[tid]);
-            s_exc[tid] = 0;
+        if (t < kExcBins && W.exc[t]) {
+            atomicAdd(&st->exc[t], (unsigned long long)W.exc[t]);
+            W.exc[t] = 0;
         }
-        if (tid < 4 && s_q[tid]) {
-            atomicAdd(&st->q[tid], s_q[tid]);
-            s_q[tid] = 0ull;
+        if (t < 4 && W.q[t]) {
+            atomicAdd(&st->q[t], W.q[t]);
+            W.q[t] = 0ull;
         }
-        for (int e = tid; e < KMAX; e += NT) {
-            if (s_spec[e]) {
-                atomicAdd(&st->spec[e], s_spec[e]);
-                s_spec[e] = 0ull;
+        for (int e = t; e < KMAX; e += 128) {
+            if (W.spec[e]) {
+                atomicAdd(&st->spec[e], W.spec[e]);
+                W.spec[e] = 0ull;
             }
         }
-        if (tid == 0) {
+        if (t == 0) {
             atomicAdd(&st->n_prop, (unsigned long long)n_here);
-            if (s_cnt[0]) atomicAdd(&st->n_acc, (unsigned long long)s_cnt[0]);
-            if (s_cnt[1]) atomicAdd(&st->n_viol, (unsigned long long)s_cnt[1]);
-            if (s_cnt[2]) atomicAdd(&st->n_dropped, (unsigned long long)s_cnt[2]);
-            if (s_cnt[3]) atomicAdd(&st->n_fallback, (unsigned long long)s_cnt[3]);
-            if (s_maxd) atomicMax(&st->maxd_key, (unsigned long long)s_maxd);
-            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
-            s_maxd = 0;
+            if (W.cnt[0]) atomicAdd(&st->n_acc, (unsigned long long)W.cnt[0]);
+            if (W.cnt[1]) atomicAdd(&st->n_viol, (unsigned long long)W.cnt[1]);
+            if (W.cnt[2]) atomicAdd(&st->n_dropped, (unsigned long long)W.cnt[2]);
+            if (W.cnt[3]) atomicAdd(&st->n_fallback, (unsigned long long)W.cnt[3]);
+            if (W.maxd) atomicMax(&st->maxd_key, (unsigned long long)W.maxd);
+            W.cnt[0] = W.cnt[1] = W.cnt[2] = W.cnt[3] = 0;
+            W.maxd = 0;
         }
-        __syncthreads();
+        wg_sync(g);
     }
     // a commit that timed out may still land: wait for it (bounded) before
     // the accumulator columns are released
-#pragma unroll
-    for (int bb = 0; bb < NBUF; ++bb)
-        if (waits_pending[bb]) (void)mbar_wait_bounded(smem_u32(&s_mbar[bb]), phase[bb]);
+    if (pending) (void)mbar_wait_bounded(mbar, phase);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid < 32) tmem_dealloc(s_tmem, tcols * NBUF);
+    if (threadIdx.x < 32) tmem_dealloc(s_tmem, tcols);
 }
 
-template <int KMAX, int NBUF>
-void fill_grid_kernels(GridKernels *t) {
-    t->main[0] = (const void *)k_sample_grid<KMAX, false, NBUF>;
-    t->main[1] = (const void *)k_sample_grid<KMAX, true, NBUF>;
-    t->nwg = NBUF;
+template <int KMAX>
+void fill_grid_kernels_nwg(GridKernels *t, int variant, const void *g0, const void *g1, int nwg) {
+    t->main[variant][0] = g0;
+    t->main[variant][1] = g1;
+    t->nwg[variant] = nwg;
+    if (variant + 1 > t->n_variants) t->n_variants = variant + 1;
     t->kmax = KMAX;
     t->ka = GridShape<KMAX>::KA;
+}
+
+// Variant v of the KMAX grid kernels with NWG warpgroups per CTA.
+template <int KMAX, int NWG>
+void fill_grid_variant(GridKernels *t, int variant) {
+    fill_grid_kernels_nwg<KMAX>(t, variant, (const void *)k_sample_grid<KMAX, false, NWG>,
+                                (const void *)k_sample_grid<KMAX, true, NWG>, NWG);
 }
 
 }  // namespace tkdv

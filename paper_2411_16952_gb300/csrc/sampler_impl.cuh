@@ -44,6 +44,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same block with the round keys given (RoundKeys: round r uses
+// rk[2r], rk[2r+1]); rk points at the run's kernel arguments, so every key is
+// a constant operand of its round.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // (2 floor(w/512) + 1) 2^-24, exact in FP32: the float 1 + m 2^-23 with
 // m = w >> 9 is built from its bits, and subtracting 1 - 2^-24 (a float) is
 // exact (Sterbenz), leaving (2m + 1) 2^-24.
@@ -197,11 +212,32 @@ struct Draw {
     float rrmax;    // largest sigma_m/sqrt(rho_m): above kOutputRr |x| outputs need rho_acc
 };
 
+// Philox keys: the key pair (key schedule computed per block) or the run's
+// round keys.
+struct KeyPair {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint4 block(uint4 c) const { return philox4x32_10(c, k0, k1); }
+};
+struct KeyRounds {
+    const uint32_t *rk;
+    __device__ __forceinline__ uint4 block(uint4 c) const { return philox4x32_10_rk(c, rk); }
+};
+
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
+template <int KMAX, bool UNIF, bool ACC = false, typename Keys = KeyPair>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act,
+                                            uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, Keys keys);
+
 template <int KMAX, bool UNIF, bool ACC = false>
 __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
                                           uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                           uint32_t k0, uint32_t k1) {
+    draw_fast_k<KMAX, UNIF, ACC>(d, sig, act, idx_lo, idx_hi, pid, KeyPair{k0, k1});
+}
+
+template <int KMAX, bool UNIF, bool ACC, typename Keys>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act,
+                                            uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, Keys keys) {
     d.nrm2 = 0.f;
     d.Sraw = 0.f;
     d.zz = 0.f;
@@ -211,7 +247,7 @@ __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const
     d.rrmax = 0.f;
 #pragma unroll
     for (int j = 0; j < (KMAX + 1) / 2; ++j) {
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, idx_lo, idx_hi, pid), k0, k1);
+        const uint4 w = keys.block(make_uint4((uint32_t)j, idx_lo, idx_hi, pid));
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
@@ -328,6 +364,10 @@ __device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, u
 __device__ __forceinline__ uint32_t accept_word(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                                 int K, uint32_t k0, uint32_t k1) {
     return philox4x32_10(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), k0, k1).x;
+}
+__device__ __forceinline__ uint32_t accept_word_rk(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, int K,
+                                                   const uint32_t *rk) {
+    return philox4x32_10_rk(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), rk).x;
 }
 
 __device__ __forceinline__ int hist_bin(float u0, float a, float b) {
@@ -576,8 +616,8 @@ __global__ void __launch_bounds__(NT, MINB)
             const unsigned long long idx = base + i;
             const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
             Draw<KMAX> dr;
-            draw_fast<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, k0, k1);
-            const uint32_t wa = accept_word(lo, hi, sc.pid, sc.K, k0, k1);
+            draw_fast_k<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, KeyRounds{A.rk.k});
+            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
             // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
             const bool tail = min(dr.wmin, wa) < kTailBucket;

@@ -45,13 +45,15 @@ struct tkdv_sampler {
     bool own_stream = false;
     DevBufs dev{};
     void *d_pts = nullptr, *d_stats = nullptr, *d_ring = nullptr, *d_ring_count = nullptr,
-         *d_refine = nullptr, *d_counters = nullptr, *d_status = nullptr;
+         *d_refine = nullptr, *d_counters = nullptr, *d_status = nullptr, *d_accs = nullptr;
     size_t rec_bytes = 0;
     TriadKernels kt{};
     GridKernels kg{};
     int grid_N = 0;
     void *d_bimg = nullptr;   // grid form: BF16 hi/lo basis image
-    size_t dyn_smem = 0;      // grid form: dynamic shared memory per CTA
+    size_t dyn_smem[kGridVariants] = {};  // grid form: dynamic shared memory per CTA of each variant
+    bool gvalid[kGridVariants] = {};      // grid form: the variant fits (TMEM, shared memory) for this grid_N
+    int gfirst = 0;                       // grid form: the default variant (the first that fits)
     float *trace = nullptr;   // grid form: optional per-proposal trace (device)
     unsigned long long trace_n = 0;
     Launch launch;
@@ -161,8 +163,8 @@ int set_form(tkdv_sampler *h, int form) {
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemcpy(h->d_pts, h->pc.data(), sizeof(PointConst) * h->n_points, cudaMemcpyHostToDevice));
     if (form == TKDV_H3_GRID_BF16X3) {
-        h->launch.threads = 128;
-        h->launch.variant = 0;
+        h->launch.variant = h->gfirst;
+        h->launch.threads = 128 * h->kg.nwg[h->gfirst];
     } else {
         h->launch.threads = 256;
         h->launch.variant = h->kmax == 128 ? 2 : 1;
@@ -172,7 +174,7 @@ int set_form(tkdv_sampler *h, int form) {
 
 const void *main_fn(const tkdv_sampler *h, int variant) {
     const int uni = h->all_uniform ? 1 : 0;
-    if (is_grid(h)) return h->kg.main[uni];
+    if (is_grid(h)) return h->kg.main[variant][uni];
     if (h->opt.sir) return h->kt.sir[uni];  // one form (256 threads)
     return h->kt.main[uni][variant];
 }
@@ -181,16 +183,22 @@ const void *main_fn(const tkdv_sampler *h, int variant) {
 // `variant` with `threads` threads: the grid form's tiles, or the triad
 // form's accept hand-off (variants 0..2; none in SIR runs and in the warp form).
 size_t main_dyn_smem(const tkdv_sampler *h, int variant, int threads) {
-    if (is_grid(h)) return h->dyn_smem;
+    if (is_grid(h)) return h->dyn_smem[variant];
     if (h->opt.sir || variant >= 3) return 0;
     return (size_t)threads * (size_t)h->kt.xfer_bytes_per_thread;
 }
 
-// TMEM columns one grid-form CTA allocates.
-int grid_tmem_cols(const tkdv_sampler *h) {
+// TMEM columns one grid-form CTA of launch variant `variant` allocates:
+// N per warpgroup (its C and S accumulators), rounded up to a power of two.
+int grid_tmem_cols(const tkdv_sampler *h, int variant) {
     int c = 32;
-    while (c < h->grid_N) c <<= 1;
-    return c * h->kg.nwg;
+    while (c < h->grid_N * h->kg.nwg[variant]) c <<= 1;
+    return c;
+}
+
+// Threads per CTA of launch variant `variant` of the current form.
+int variant_threads(const tkdv_sampler *h, int variant) {
+    return is_grid(h) ? 128 * h->kg.nwg[variant] : kTriadVariantThreads[variant];
 }
 
 // Largest number of resident CTAs per SM for the handle's form.
@@ -209,12 +217,12 @@ int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
         CK(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, h->device));
         CK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->device));
-        const size_t smem_blk = h->dyn_smem + fa.sharedSizeBytes + (size_t)resv;
+        const size_t smem_blk = h->dyn_smem[variant] + fa.sharedSizeBytes + (size_t)resv;
         const int regs_thr = (fa.numRegs + 7) / 8 * 8;
         const int regs_blk = ((regs_thr * 32 + 255) / 256 * 256) * ((threads + 31) / 32);
         int by_smem = (int)((size_t)smem_sm / smem_blk);
         int by_regs = regs_blk > 0 ? regs_sm / regs_blk : 1;
-        int by_tmem = 512 / grid_tmem_cols(h);
+        int by_tmem = 512 / grid_tmem_cols(h, variant);
         const int own = std::max(1, std::min(by_smem, std::min(by_regs, by_tmem)));
         if (std::getenv("TKDV_AUTOTUNE_LOG"))
             std::fprintf(stderr, "tkdv occupancy: query %d, shared memory %d, registers %d (%d/thread), TMEM %d\n",
@@ -248,9 +256,13 @@ int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned l
         a.count[p] = count[p];
         total += count[p];
     }
-    // about 8 chunks per persistent CTA, between 1 and 64 proposals per thread
-    const unsigned long long thr = (unsigned long long)h->launch.threads;
-    unsigned long long target = (total + 8ull * h->launch.ctas - 1) / (8ull * h->launch.ctas);
+    // about 8 chunks per persistent worker (a CTA of the triad form, a
+    // warpgroup of the grid form), between 1 and 64 proposals per thread
+    const bool grid = is_grid(h);
+    const unsigned long long thr = grid ? 128ull : (unsigned long long)h->launch.threads;
+    const unsigned long long workers =
+        (unsigned long long)h->launch.ctas * (grid ? (unsigned long long)h->kg.nwg[h->launch.variant] : 1ull);
+    unsigned long long target = (total + 8ull * workers - 1) / (8ull * workers);
     target = (target + thr - 1) / thr * thr;
     target = std::max(thr, std::min(thr * 64ull, target));
     a.chunk = (uint32_t)target;
@@ -266,6 +278,7 @@ int build_args(tkdv_sampler *h, const unsigned long long *idx0, const unsigned l
     a.trace_n = h->trace ? h->trace_n : 0ull;
     h->key0 = (uint32_t)seed;
     h->key1 = (uint32_t)(seed >> 32);
+    a.rk = round_keys(h->key0, h->key1);
     return TKDV_OK;
 }
 
@@ -285,7 +298,7 @@ int build_graph(tkdv_sampler *h) {
     ms.dst = h->d_counters;
     ms.value = 0;
     ms.elementSize = 4;
-    ms.width = 2;
+    ms.width = 4;
     ms.height = 1;
     ms.pitch = 0;
     cudaGraphNode_t n_ms;
@@ -341,7 +354,7 @@ int enqueue(tkdv_sampler *h) {
         CK(cudaGraphLaunch(h->exec, h->stream));
         return TKDV_OK;
     }
-    CK(cudaMemsetAsync(h->d_counters, 0, 8, h->stream));
+    CK(cudaMemsetAsync(h->d_counters, 0, 16, h->stream));
     const unsigned char *bimg = (const unsigned char *)h->d_bimg;
     int gN = h->grid_N;
     void *margs[] = {&h->dev, &h->args, &h->key0, &h->key1, &bimg, &gN};
@@ -378,7 +391,7 @@ void free_all(tkdv_sampler *h) {
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (void *p : {h->d_pts, h->d_stats, h->d_ring, h->d_ring_count, h->d_refine, h->d_counters, h->d_status,
-                    h->d_bimg})
+                    h->d_bimg, h->d_accs})
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -520,21 +533,36 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
             grid_kernels_k64(&h->kg);
         h->grid_ok = true;
         h->launch.form = TKDV_H3_GRID_BF16X3;
-        h->launch.variant = 0;
         h->pc = h->pc_grid;
-        h->launch.threads = 128;
-        const size_t btile = (size_t)gridN * h->kg.ka * 2, atile = (size_t)128 * h->kg.ka * 2;
-        h->dyn_smem = 2 * btile + (size_t)h->kg.nwg * 2 * atile + 1024;
-        for (int u = 0; u < 2; ++u) {
-            e = cudaFuncSetAttribute(h->kg.main[u], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem);
-            if (e == cudaSuccess)  // the largest shared-memory carve-out, so that two CTAs fit on an SM
-                e = cudaFuncSetAttribute(h->kg.main[u], cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-            if (e != cudaSuccess) {
-                h->err = std::string("grid kernel shared memory: ") + cudaGetErrorString(e);
-                return bail(TKDV_ERR_CUDA);
+        const size_t btile = (size_t)(gridN / 2) * h->kg.ka * 2, atile = (size_t)128 * h->kg.ka * 2;
+        // a variant fits if its warpgroups' accumulators (N columns each) fit
+        // the 512 TMEM columns of an SM and its tiles the shared memory
+        int smem_optin = 0;
+        e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        h->gfirst = -1;
+        for (int v = 0; v < h->kg.n_variants && e == cudaSuccess; ++v) {
+            h->dyn_smem[v] = 2 * btile + (size_t)h->kg.nwg[v] * 2 * atile + 1024;
+            h->gvalid[v] = h->kg.nwg[v] * gridN <= 512 && h->dyn_smem[v] + 8192 <= (size_t)smem_optin;
+            if (!h->gvalid[v]) continue;
+            if (h->gfirst < 0) h->gfirst = v;
+            for (int u = 0; u < 2 && e == cudaSuccess; ++u) {
+                e = cudaFuncSetAttribute(h->kg.main[v][u], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)h->dyn_smem[v]);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(h->kg.main[v][u], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
             }
         }
+        if (e != cudaSuccess) {
+            h->err = std::string("grid kernel shared memory: ") + cudaGetErrorString(e);
+            return bail(TKDV_ERR_CUDA);
+        }
+        if (h->gfirst < 0) {
+            h->err = "no grid-form launch fits this grid_N";
+            return bail(TKDV_ERR_UNSUPPORTED);
+        }
+        h->launch.variant = h->gfirst;
+        h->launch.threads = 128 * h->kg.nwg[h->gfirst];
         std::vector<unsigned char> img(2 * btile);
         build_grid_image(h->K, h->kg.kmax, h->kg.ka, gridN, img.data());
         e = cudaMalloc(&h->d_bimg, img.size());
@@ -560,7 +588,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     if ((rc = alloc(&h->d_ring, h->rec_bytes * cap))) return bail(rc);
     if ((rc = alloc(&h->d_ring_count, 8))) return bail(rc);
     if ((rc = alloc(&h->d_refine, sizeof(RefineItem) * (size_t)kRefineCap))) return bail(rc);
-    if ((rc = alloc(&h->d_counters, 8))) return bail(rc);
+    if ((rc = alloc(&h->d_counters, 16))) return bail(rc);
     if ((rc = alloc(&h->d_status, 4))) return bail(rc);
     if (opt->cuda_stream) {
         h->stream = (cudaStream_t)opt->cuda_stream;
@@ -575,7 +603,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     e = cudaMemcpy(h->d_pts, h->pc.data(), sizeof(PointConst) * n_points, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(StatBlock) * n_points);
     if (e == cudaSuccess) e = cudaMemset(h->d_ring_count, 0, 8);
-    if (e == cudaSuccess) e = cudaMemset(h->d_counters, 0, 8);
+    if (e == cudaSuccess) e = cudaMemset(h->d_counters, 0, 16);
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 4);
     if (e != cudaSuccess) {
         h->err = std::string("initialising device buffers: ") + cudaGetErrorString(e);
@@ -593,6 +621,22 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
     h->dev.refine_cap = kRefineCap;
     h->dev.sir = opt->sir;
     if ((rc = set_default_launch(h))) return bail(rc);
+    if (h->grid_ok) {
+        // one slab of accepted draws per warp of the largest grid-form launch
+        size_t warps = 0;
+        const int form0 = h->launch.form;
+        h->launch.form = TKDV_H3_GRID_BF16X3;
+        for (int v = 0; v < h->kg.n_variants; ++v) {
+            if (!h->gvalid[v]) continue;
+            int nb = 0;
+            if ((rc = max_ctas_per_sm(h, v, variant_threads(h, v), &nb))) return bail(rc);
+            warps = std::max(warps, (size_t)std::max(nb, 1) * h->num_sms * h->kg.nwg[v] * 4);
+        }
+        h->launch.form = form0;
+        if ((rc = alloc(&h->d_accs, warps * kAcceptSlab * sizeof(AcceptItem)))) return bail(rc);
+        h->dev.accs = (AcceptItem *)h->d_accs;
+        h->dev.acc_slab = kAcceptSlab;
+    }
     *out = h;
     return TKDV_OK;
 }
@@ -814,11 +858,12 @@ int sampler_autotune(tkdv_sampler *h, uint64_t calib_proposals, double *best_us)
             if (rcf) return rcf;
         }
         std::vector<int> var_list;
-        for (int v = 0; v < h->kt.n_variants; ++v) var_list.push_back(v);
-        if (is_grid(h)) var_list = {0};
+        const int nvar = is_grid(h) ? h->kg.n_variants : h->kt.n_variants;
+        for (int v = 0; v < nvar; ++v)
+            if (!is_grid(h) || h->gvalid[v]) var_list.push_back(v);
         if (h->opt.sir) var_list = {1};
         for (int var : var_list) {
-            const int thr = is_grid(h) ? 128 : kTriadVariantThreads[var];
+            const int thr = variant_threads(h, var);
             int nb = 0;
             const int rc0 = max_ctas_per_sm(h, var, thr, &nb);
             if (rc0) return rc0;
@@ -863,13 +908,13 @@ int sampler_set_launch(tkdv_sampler *h, int variant, int ctas_per_sm) {
     if (!h || ctas_per_sm < 0) return TKDV_ERR_INVALID_ARG;
     bool ok;
     if (is_grid(h))
-        ok = variant == 0;
+        ok = variant >= 0 && variant < h->kg.n_variants && h->gvalid[variant];
     else if (h->opt.sir)
         ok = variant == 1;
     else
         ok = variant >= 0 && variant < h->kt.n_variants;
     if (!ok) return fail(h, TKDV_ERR_INVALID_ARG, "no such launch variant for this handle's form");
-    const int thr = is_grid(h) ? 128 : kTriadVariantThreads[variant];
+    const int thr = variant_threads(h, variant);
     int nb = 0;
     const int rc = max_ctas_per_sm(h, variant, thr, &nb);
     if (rc) return rc;

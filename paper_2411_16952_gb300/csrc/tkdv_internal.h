@@ -16,6 +16,9 @@ constexpr int kMaxPoints = 64;
 constexpr int kHistBins = 256;
 constexpr int kExcBins = 26;  // exceed-bin e = number of thresholds 0.25 i sigma0 below u0
 constexpr uint32_t kRefineCap = 1u << 22;
+// grid form: accepted draws one warp holds until the end of its chunk (a
+// chunk has at most 64 proposals per thread, so 2048 per warp)
+constexpr uint32_t kAcceptSlab = 2048;
 
 // Fixed-point scales of the u0^p moment sums (exact 64-bit integer sums).
 constexpr float kQ1 = 268435456.0f;  // 2^28
@@ -80,6 +83,13 @@ struct RefineItem {
     uint32_t pad;
 };
 
+// An accepted draw of the grid form waiting for its outputs.
+struct AcceptItem {
+    unsigned long long idx;
+    float T;      // H3 / (2 pi (E0/2pi)^{3/2}) from the grid contraction
+    float delta;  // log f/(Mg) of the FP32 path
+};
+
 // Device buffers of one handle.
 struct DevBufs {
     const PointConst *pts;
@@ -93,12 +103,30 @@ struct DevBufs {
     uint32_t rec_bytes;
     uint32_t refine_cap;
     int sir;  // 1: the FP64 pass draws SIR copy numbers instead of accept bits
+    AcceptItem *accs;   // grid form: one slab of acc_slab accepted draws per warp of the launch
+    uint32_t acc_slab;
 };
 
 constexpr uint32_t kStatusRefineOverflow = 1u;
 constexpr uint32_t kStatusDeadline = 2u;
 constexpr uint32_t kStatusMbarTimeout = 4u;
 constexpr uint32_t kStatusBadArg = 8u;
+
+// Round keys of Philox4x32-10 for the run's key (k0, k1): round r uses
+// (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85) mod 2^32, r = 0..9.  Passed with the
+// kernel arguments, so that the rounds take their keys as constant operands
+// instead of recomputing the key schedule for every block.
+struct RoundKeys {
+    uint32_t k[20];
+};
+inline RoundKeys round_keys(uint32_t k0, uint32_t k1) {
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return rk;
+}
 
 // Arguments of one run (passed by value; the graph updates them per run).
 struct RunArgs {
@@ -110,6 +138,7 @@ struct RunArgs {
     unsigned long long deadline_ns;          // 0: none; else per-CTA budget in ns
     float *trace;                            // grid form: (log f/(Mg), T) of point 0's first trace_n
     unsigned long long trace_n;              // proposals, or null
+    RoundKeys rk;                            // Philox round keys of the run's seed
 };
 
 // Kernel table of one KMAX instantiation of the triad sampler.
@@ -135,17 +164,20 @@ void triad_kernels_k64_lane(TriadKernels *t);  // variants 3..5 of the 64-mode t
 void triad_kernels_k128(TriadKernels *t);
 
 // Kernel table of one KMAX instantiation of the grid (tensor-core) sampler.
+constexpr int kGridVariants = 3;
 struct GridKernels {
-    const void *main[2];  // [uniform]
-    int nwg;              // tile buffers (TMEM accumulators) per 128-thread CTA
-    int kmax;             // modes per tile row half
-    int ka;               // contraction length (multiple of 64)
+    const void *main[kGridVariants][2];  // [variant][uniform]
+    int nwg[kGridVariants];              // warpgroups (tiles, TMEM accumulator pairs) per CTA of each variant
+    int n_variants;
+    int kmax;                            // modes per part of a tile row
+    int ka;                              // contraction length (multiple of 64): [cosine part | sine part]
 };
 void grid_kernels_k16(GridKernels *t);
 void grid_kernels_k32(GridKernels *t);
 void grid_kernels_k64(GridKernels *t);
-// BF16 hi/lo image of the grid basis, already in the 128B-swizzled K-major
-// layout of shared memory: bytes [0, N*KA*2) hi, [N*KA*2, 2*N*KA*2) lo.
+// BF16 hi/lo image of the grid basis (N/2 mirror pairs of grid points as
+// rows), already in the 128B-swizzled K-major layout of shared memory: bytes
+// [0, (N/2)*KA*2) hi, [(N/2)*KA*2, N*KA*2) lo.
 void build_grid_image(int K, int kmax, int ka, int N, unsigned char *out);
 
 constexpr int kTriadVariantThreads[6] = {128, 256, 256, 128, 256, 256};

@@ -151,6 +151,7 @@ extern "C" int sampler_run_static(int K, const tkdv_point *point, uint64_t idx0,
     A.chunk_prefix[0] = 0;
     A.chunk_prefix[1] = (uint32_t)((n_proposals + chunk - 1) / chunk);
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    A.rk = round_keys(k0, k1);
 
     // The array keeps the previous call's contents: clear the header (the
     // statistics, counters and status must start at zero), then upload the
