@@ -55,12 +55,14 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
     triad: the symmetric double sum of Eq. (42) (4 FMA per pair k < n-k, 3 for
     the middle term, 4 for the outer update).
     grid: BF16 hi/lo split and shared-memory store of the 2K values (3.5 per
-    value), the cube-and-sum of the N grid values (2 per value) and their
-    TMEM loads (1 per 32)."""
+    value), the sum of 2 C (C^2 + 3 S^2) over the N/2 mirror pairs of grid
+    points (two packed FP32x2 instructions per two pairs and two
+    multiplications: 1 per grid point) and the TMEM loads of C and S (1 per
+    16 columns)."""
     blocks = (K + 1) // 2 + 1
     common = 40 * blocks + 20 * K + 4 * K + 40
     if form == "grid":
-        return int(common + 3.5 * 2 * K + 2 * grid_N + grid_N // 32)
+        return int(common + 3.5 * 2 * K + grid_N + grid_N // 16)
     triad = sum(4 * ((n - 1) // 2) + (3 if n % 2 == 0 else 0) + 4 for n in range(2, K + 1))
     return common + triad
 
@@ -71,8 +73,8 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (167680.0 / (8 * 4194304), "ncu --set full capture prof_grid26 (k_sample_grid<32,0,1>)"),
-    "triad": (128256.0 / (8 * 4194304), "ncu --set full capture prof_triad26 (k_sample_triad<32,0,256,1,0,1>)"),
+    "grid": (None, "not captured since the kernel last changed"),
+    "triad": (None, "not captured since the kernel last changed"),
 }
 
 
@@ -83,9 +85,11 @@ def alu_peak(n_sms, peaks):
 
 
 def tensor_flops_per_proposal(K: int, grid_N: int) -> int:
-    """Three BF16 products of a 2K-padded-to-64 row with the 2K x N basis."""
-    ka = (2 * K + 63) // 64 * 64
-    return 3 * 2 * ka * grid_N
+    """The mirror-pair contraction as issued: three BF16 products (hi hi, hi lo,
+    lo hi) of the cosine and of the sine part of a row (K modes rounded up to
+    a 16-column MMA step) with an N/2-column basis."""
+    kpad = (K + 15) // 16 * 16
+    return 3 * 2 * (2 * kpad) * (grid_N // 2)
 
 
 class Clocks:
@@ -275,6 +279,161 @@ def _oracle_envelope(K, bp, E0, r, pt):
     return O.log_M(pt, 0)
 
 
+def train_learned(T, K, pts3, grid_N, n_accept, steps, tau, seed, stream, keep=False):
+    """Train the learned proposal on n_accept accepted samples per point of
+    pts3 [(beta', E0, C3/C2), ...] (paper-proposal sampler, grid form), with
+    the tempered loss J_tau.  Per point the corrections are kept only where
+    the learned proposal's envelope is below the paper's (its acceptance is
+    Prod w_k Z / M with Prod w_k unchanged by mean-zero corrections, so the
+    gain is exactly exp(log M_paper - log M_learned)); elsewhere the point
+    falls back to the paper's Sigma.  Returns (corrections P x K, info, the
+    network handle if keep else None)."""
+    from paper_2411_16952_gb300 import learned as L
+    t0 = time.perf_counter()
+    mlp, corr, hist, rows = L.train(K, pts3, n_accept=n_accept, steps=steps, lr=2e-2, tau=tau, seed=1,
+                                    sampler_seed=seed, stream=stream, h3_mode=T.H3_GRID_BF16X3, grid_N=grid_N)
+    t_train = time.perf_counter() - t0
+    info = []
+    for i, p3 in enumerate(pts3):
+        gain, lm_p, lm_l = L.predicted_gain(K, p3, corr[i])
+        fallback = not gain > 1.0
+        info.append({"beta_p": p3[0], "E0": p3[1], "r": p3[2], "gain_trained": gain,
+                     "gain": 1.0 if fallback else gain, "fallback_to_paper": fallback,
+                     "max_abs_c": float(np.max(np.abs(corr[i])))})
+        if fallback:
+            corr[i] = 0.0
+    if not keep:
+        L.close(mlp)
+        mlp = None
+    return corr, {"train_seconds": t_train, "accepted_rows_per_point": [int(v) for v in rows],
+                  "tau": tau, "steps": steps, "loss_first_last": [float(hist[0]), float(hist[-1])],
+                  "points": info}, mlp
+
+
+def k64_pipeline(T, args, stream, peaks, n_sms, rank):
+    """The 64-mode pipeline (learned proposal + BF16 hi/lo grid form, N = 256):
+    the upstream ensemble (2^30 proposals, one run), then the downstream beta'
+    by bisection on the matching statistic (here the ensemble mean of
+    S = H2/E0), 16 candidates per step in one persistent launch of 2^30
+    proposals.  Every run is timed with CUDA events on the sampler's stream;
+    the per-point precompute (alpha*, envelope search) of each step's
+    candidates is host work outside the events and is reported apart."""
+    from paper_2411_16952_gb300 import learned as L
+    from paper_2411_16952_gb300 import matching as MT
+    from paper_2411_16952_gb300 import workloads
+    import torch
+    pw = workloads.pipeline_k64()
+    K, N, E0 = pw["K"], pw["grid_N"], pw["E0"]
+    up = (pw["beta_up"], E0, pw["r_up"])
+    train_pts = [up] + [(float(b), E0, pw["r_down"]) for b in np.linspace(pw["lo"], pw["hi"], 7)]
+    corr, info, mlp = train_learned(T, K, train_pts, N, pw["learn_accept"], args.learn_steps, args.learn_tau,
+                                    rank + 3000, stream, keep=True)
+    runs = []
+
+    def timed_run(points, budget, seed):
+        t_host = time.perf_counter()
+        S = T.Sampler(K, points, h3_mode=T.H3_GRID_BF16X3, grid_N=N, sample_capacity=1 << 16, stream=stream)
+        S.run_ranges([1 << 62] * len(points), [1] * len(points), seed)  # builds the run's graph
+        S.sync()
+        S.reset()
+        t_host = time.perf_counter() - t_host
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.run(budget, seed)
+        e1.record(stream)
+        st = S.stats()
+        S.close()
+        ms = e0.elapsed_time(e1)
+        runs.append({"points": len(points), "proposals": budget * len(points), "ms": ms, "host_setup_s": t_host,
+                     "accepted": int(sum(s["n_accepted"] for s in st))})
+        return st
+
+    try:
+        st_up = timed_run([T.make_point(*up, T.PROPOSAL_LEARNED, point_id=rank * 4096,
+                                        log_var_correction=corr[0])], pw["n_up"], 11)[0]
+        target = MT.mean_S(st_up, K)
+
+        def run_batch(betas, pid0, n, seed):
+            pts3 = [(float(b), E0, pw["r_down"]) for b in betas]
+            c = L.infer(mlp, K, pts3)
+            points = [T.make_point(b, e, r, T.PROPOSAL_LEARNED, point_id=rank * 4096 + 1 + pid0 + j,
+                                   log_var_correction=c[j]) for j, (b, e, r) in enumerate(pts3)]
+            return timed_run(points, n, seed)
+
+        res = MT.bisect_beta(K, E0, pw["r_down"], MT.mean_S, target, pw["lo"], pw["hi"],
+                             n_candidates=pw["n_candidates"], n_steps=pw["steps"],
+                             proposals_per_candidate=pw["n_cand"], seed=21, run_batch=run_batch)
+        err = None
+    except (ValueError, T.TkdvError) as e:  # the statistic did not bracket the target, or a run failed
+        res, err = None, str(e)
+    finally:
+        L.close(mlp)
+    t_s = sum(r["ms"] for r in runs) / 1e3
+    props = sum(r["proposals"] for r in runs)
+    acc = sum(r["accepted"] for r in runs)
+    pps = props / t_s if t_s > 0 else 0.0
+    ops = alg_ops_per_proposal(K, "grid", N)
+    tf = tensor_flops_per_proposal(K, N) * pps / 1e12
+    tpk = float(peaks.get("bf16_tflops_sustained", 1735.3))
+    out = {"workload": pw["name"], "K": K, "grid_N": N, "form": "grid_bf16x3_learned", "error": err,
+           "proposals_per_s": pps, "accepted_per_s": acc / t_s if t_s > 0 else 0.0, "runs": runs,
+           "roofline": {"alu": {"ops_per_proposal": ops, "achieved": ops * pps / 1e12, "peak": alu_peak(n_sms, peaks),
+                                "unit": "Tops/s", "frac": ops * pps / 1e12 / alu_peak(n_sms, peaks)},
+                        "tensor": {"flops_per_proposal": tensor_flops_per_proposal(K, N), "achieved_tflops": tf,
+                                   "peak_tflops": tpk, "frac": tf / tpk,
+                                   "note": "mirror-pair BF16 hi/lo x3 contraction flops over the sampler runs' "
+                                           "duration, against the sustained cuBLAS BF16 peak"}},
+           "learned": {"train_seconds": info["train_seconds"], "tau": info["tau"],
+                       "accepted_rows_per_point": info["accepted_rows_per_point"],
+                       "gain_exact": [q["gain"] for q in info["points"]],
+                       "fallback_to_paper": [q["fallback_to_paper"] for q in info["points"]]}}
+    if runs:
+        n_up = st_up["n_accepted"]
+        sig0 = math.sqrt(E0 / math.pi)
+        out["upstream"] = {"beta_p": up[0], "r": up[2], "proposals": runs[0]["proposals"], "ms": runs[0]["ms"],
+                           "accepted": n_up, "acceptance": n_up / runs[0]["proposals"], "mean_S": MT.mean_S(st_up, K),
+                           "u0": {"mean": st_up["mean"], "var": st_up["var"], "skew": st_up["skew"],
+                                  "kurt": st_up["kurt"]},
+                           "exceed_2_3_4_sigma0": [int(st_up["exceed"][8]), int(st_up["exceed"][12]),
+                                                   int(st_up["exceed"][16])],
+                           "sigma0": sig0, "hist_bins_nonzero": int(np.count_nonzero(st_up["hist"])),
+                           "envelope_violations": int(st_up["n_envelope_violations"])}
+    if res is not None:
+        out["downstream"] = {"r": pw["r_down"], "beta_p_found": res["beta"], "bracket": list(res["bracket"]),
+                             "target_mean_S": MT.mean_S(st_up, K), "steps": pw["steps"],
+                             "candidates_per_step": pw["n_candidates"],
+                             "proposals_per_step": pw["n_candidates"] * pw["n_cand"],
+                             "ms_per_step": [r["ms"] for r in runs[1:]],
+                             "last_step": {"betas": [float(b) for b in res["history"][-1][0]],
+                                           "mean_S": [float(v) for v in res["history"][-1][1]]}}
+    return out
+
+
+def measured_gain(st_paper, st_learned, info):
+    """Per point: the learned proposal's acceptance over the paper's, measured
+    (with its standard error; both from the timed runs, independent streams
+    assumed) against the exact value, and the u(0) mean, variance and
+    skewness of the two ensembles (the same Gibbs measure: within 3 SE)."""
+    out = []
+    for sp, sl, pi in zip(st_paper, st_learned, info):
+        ap, al = sp["n_accepted"] / sp["n_proposals"], sl["n_accepted"] / sl["n_proposals"]
+        ratio = al / ap if ap > 0 else float("nan")
+        se = ratio * math.sqrt(1.0 / max(sp["n_accepted"], 1) + 1.0 / max(sl["n_accepted"], 1))
+        nn = max(min(sp["n_accepted"], sl["n_accepted"]), 1)
+        se_mean = 2 * math.sqrt(sp["var"] / nn)
+        se_var = 2 * sp["var"] * math.sqrt(max(sp["kurt"] - 1.0, 1.0) / nn)
+        se_skew = 2 * math.sqrt(6.0 / nn)
+        out.append({"beta_p": pi["beta_p"], "gain_exact": pi["gain"], "gain_measured": ratio, "gain_se": se,
+                    "within_4se": abs(ratio - pi["gain"]) <= 4 * se,
+                    "u0_mean": [sp["mean"], sl["mean"]], "u0_var": [sp["var"], sl["var"]],
+                    "u0_skew": [sp["skew"], sl["skew"]],
+                    "stats_within_3se": bool(abs(sp["mean"] - sl["mean"]) <= 1.5 * se_mean and
+                                             abs(sp["var"] - sl["var"]) <= 1.5 * se_var and
+                                             abs(sp["skew"] - sl["skew"]) <= 1.5 * se_skew),
+                    "envelope_violations": int(sl["n_envelope_violations"])})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,9 +447,14 @@ def main():
     ap.add_argument("--ref-proposals", type=int, default=1 << 22)
     ap.add_argument("--ref-exact-envelope", action="store_true")
     ap.add_argument("--forms", default="", help="comma list of forms to time (default: all)")
-    ap.add_argument("--learn-accept", type=int, default=1 << 14, help="accepted samples per point to train on")
-    ap.add_argument("--learn-steps", type=int, default=200)
+    ap.add_argument("--learn-accept", type=int, default=1 << 20, help="accepted samples per point to train on")
+    ap.add_argument("--learn-steps", type=int, default=300)
+    ap.add_argument("--learn-tau", type=float, default=0.5,
+                    help="temperature of the training loss J_tau (0: the plain mean, KL(f || g))")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-learn-accept", type=int, default=1 << 14,
+                    help="64-point batch: accepted samples per point to train its network on")
+    ap.add_argument("--no-k64", action="store_true", help="skip the 64-mode pipeline")
     ap.add_argument("--no-k128", action="store_true", help="skip the K = 128 measurement")
     ap.add_argument("--k128-n", type=int, default=1 << 24, help="K = 128: proposals per point and step")
     args = ap.parse_args()
@@ -334,18 +498,11 @@ def main():
     if "grid_bf16x3_learned" in forms:
         # the learned proposal is trained (outside the timed region) on accepted
         # samples of the same points, generated by the paper-proposal sampler
-        from paper_2411_16952_gb300 import learned as L
         pts3 = [(bp, E0, r) for bp, r, _ in pts]
-        t_tr = time.perf_counter()
-        mlp, corr, hist, rows = L.train(K, pts3, n_accept=args.learn_accept, steps=args.learn_steps,
-                                        lr=2e-2, tau=0.0, seed=1, sampler_seed=rank + 1000, stream=stream)
-        L.close(mlp)
-        gains = [L.predicted_gain(K, p3, corr[i])[0] for i, p3 in enumerate(pts3)]
-        learned_info = {"train_seconds": time.perf_counter() - t_tr, "accepted_rows_per_point": rows.tolist(),
-                        "loss_first_last": [float(hist[0]), float(hist[-1])], "steps": args.learn_steps,
-                        "predicted_acceptance_gain": gains,
-                        "max_abs_correction": float(np.max(np.abs(corr)))}
+        corr, learned_info, _ = train_learned(T, K, pts3, gN, args.learn_accept, args.learn_steps, args.learn_tau,
+                                              rank + 1000, stream)
     results = {}
+    stats_by_form = {}
     windows = []
     for fname, (mode, prop) in forms.items():
         if prop == T.PROPOSAL_LEARNED:
@@ -378,6 +535,7 @@ def main():
         windows.append((t_begin, dt.datetime.now()))
         step_ms = [a.elapsed_time(b_) for a, b_ in evs]
         st = S.stats()
+        stats_by_form[fname] = st
         acc = sum(s["n_accepted"] for s in st)
         prop_n = sum(s["n_proposals"] for s in st)
         refined = sum(s["n_refined"] for s in st)
@@ -415,6 +573,9 @@ def main():
         S.close()
         results[fname] = res
     clocks = clk.stop(windows[0][0], windows[-1][1])
+    if learned_info is not None and "grid_bf16x3_paper" in stats_by_form:
+        learned_info["measured"] = measured_gain(stats_by_form["grid_bf16x3_paper"],
+                                                 stats_by_form["grid_bf16x3_learned"], learned_info["points"])
 
     # the 64-point batch (uneven budgets 2^18..2^26, one persistent launch)
     batch = None
@@ -423,12 +584,23 @@ def main():
         bw = workloads.batch_k32()
         bpts = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]), T.PROPOSAL_PAPER,
                              point_id=rank * 64 + p) for p in range(64)]
-        # both forms: the batch's acceptances reach 4 %, where the grid form's
-        # per-accept redraw weighs more than on the headline workload
+        # the triad form, the grid form with the paper's Sigma, and the grid
+        # form with the learned proposal (a network trained on the batch's
+        # own points, the paper's Sigma where it does not lower the envelope)
         bforms = {}
-        for best_form in [f for f in ("triad_f32_paper", "grid_bf16x3_paper") if f in results]:
+        bcorr, binfo = None, None
+        if "grid_bf16x3_learned" in forms:
+            b3 = [(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p])) for p in range(64)]
+            bcorr, binfo, _ = train_learned(T, bw["K"], b3, 128, args.batch_learn_accept, args.learn_steps,
+                                            args.learn_tau, rank + 2000, stream)
+        for best_form in [f for f in ("triad_f32_paper", "grid_bf16x3_paper", "grid_bf16x3_learned") if f in results]:
             bmode = T.H3_GRID_BF16X3 if best_form.startswith("grid") else T.H3_TRIAD_F32
-            SB = T.Sampler(bw["K"], bpts, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,
+            pts_b = bpts
+            if best_form.endswith("learned"):
+                pts_b = [T.make_point(float(bw["beta_p"][p]), float(bw["E0"][p]), float(bw["r"][p]),
+                                      T.PROPOSAL_LEARNED, point_id=rank * 64 + p, log_var_correction=bcorr[p])
+                         for p in range(64)]
+            SB = T.Sampler(bw["K"], pts_b, h3_mode=bmode, grid_N=128 if bmode == T.H3_GRID_BF16X3 else 0,
                            sample_capacity=1 << 22, stream=stream)
             if not args.no_autotune:
                 SB.autotune(1 << 20)
@@ -451,11 +623,21 @@ def main():
             bacc = sum(s["n_accepted"] for s in bst)
             bforms[best_form] = {"proposals_per_step": bprop // args.steps, "ms_per_step": bms,
                                  "proposals_per_s": bprop / (bms * args.steps / 1e3),
-                                 "accepted_per_s": bacc / (bms * args.steps / 1e3), "launch": SB.launch_config()}
+                                 "accepted_per_s": bacc / (bms * args.steps / 1e3), "launch": SB.launch_config(),
+                                 "envelope_violations": int(sum(s["n_envelope_violations"] for s in bst))}
             SB.close()
         if bforms:
-            best_form = max(bforms, key=lambda f: bforms[f]["proposals_per_s"])
+            best_form = max(bforms, key=lambda f: bforms[f]["accepted_per_s"])
             batch = dict(bforms[best_form], workload=bw["name"], form=best_form, forms=bforms)
+            if binfo is not None:
+                g = [q["gain"] for q in binfo["points"]]
+                batch["learned"] = {"train_seconds": binfo["train_seconds"], "tau": binfo["tau"],
+                                    "accepted_rows_per_point_min": min(binfo["accepted_rows_per_point"]),
+                                    "gain_exact_min_median_max": [min(g), float(np.median(g)), max(g)],
+                                    "points_falling_back_to_paper": sum(q["fallback_to_paper"] for q in binfo["points"])}
+            if "triad_f32_paper" in bforms and "grid_bf16x3_learned" in bforms:
+                batch["learned_grid_vs_plain_fp32"] = (bforms["grid_bf16x3_learned"]["accepted_per_s"] /
+                                                       bforms["triad_f32_paper"]["accepted_per_s"])
 
     # K = 128 (one warp per four proposals, the cutoff of Fig. 7): eight points
     k128 = None
@@ -497,6 +679,11 @@ def main():
                         "kernel": "k_sample_warp", "note": "same op count and peak as the headline roofline"}}
         SK.close()
 
+    # the 64-mode pipeline (learned + grid form, bisection of the downstream beta')
+    k64 = None
+    if not args.no_k64 and ws == 1 and "grid_bf16x3_learned" in forms:
+        k64 = k64_pipeline(T, args, stream, peaks, n_sms, rank)
+
     h = results[headline]
     form_kind = "grid" if headline.startswith("grid") else "triad"
     ops = alg_ops_per_proposal(K, form_kind, gN)
@@ -527,7 +714,7 @@ def main():
         "headline_form": headline, "forms": results,
         "vs_plain_fp32": h["accepted_per_s"] / results["triad_f32_paper"]["accepted_per_s"]
         if "triad_f32_paper" in results else None,
-        "learned": learned_info, "batch_64pts": batch, "k128": k128,
+        "learned": learned_info, "batch_64pts": batch, "k128": k128, "k64_pipeline": k64,
         "config": {"workload": wl["name"], "K": K, "grid_N": gN, "points": len(pts),
                    "proposals_per_point_per_step": n,
                    "proposal": "learned" if headline.endswith("learned") else "paper",

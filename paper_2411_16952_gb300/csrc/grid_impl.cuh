@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(128 * NWG, 1)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int m = 2 * j + h;
-                        const float s = UNIF ? W.act[m] : W.sig[m];
+                        const float act = W.act[m];  // 1 for modes up to K, else 0
+                        const float s = UNIF ? act : W.sig[m];
                         float rho, xm, ym, rr;
                         box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
                         wmin = min(wmin, h ? w.z : w.x);
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                         const float sk = (s * s) * rho;
                         nrm2 += sk;
                         Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
-                        zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
+                        zz = fmaf(act, rho, zz);  // the active modes' squared radii
                     }
                 }
                 uint4 hx, lx, hy, ly;
@@ -484,9 +485,8 @@ __global__ void __launch_bounds__(128 * NWG, 1)
             slot0 = __shfl_sync(0xffffffffu, slot0, 0);
             if (has) {
                 const AcceptItem it = slab[b0 + lane];
-                Draw<KMAX> dr;
-                draw_fast<KMAX, UNIF, true>(dr, W.sig, W.act, (uint32_t)it.idx, (uint32_t)(it.idx >> 32), sc.pid, k0,
-                                            k1);
+                const uint32_t ilo = (uint32_t)it.idx, ihi = (uint32_t)(it.idx >> 32);
+                const DrawSums dr = acc_draw_sums<KMAX, UNIF>(W.sig, W.act, ilo, ihi, sc.pid, k0, k1);
                 const float inv2 = 1.f / dr.nrm2;
                 const float inv = rsqrtf(dr.nrm2);
                 const float u0 = sc.u0s * dr.u0raw * inv;
@@ -497,13 +497,16 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 atomicAdd(&W.q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
                 atomicAdd(&W.q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
                 atomicAdd(&W.q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
-                tally_spectrum<KMAX>(W.spec, dr.x, dr.y, inv2, sc.K);
                 const unsigned long long slot = slot0 + __popc(mh & ((1u << lane) - 1u));
-                if (slot < B.ring_cap)
-                    write_record<KMAX>(B.ring + slot * B.rec_bytes, it.idx, (uint32_t)p, 0u, sc.E0 * (dr.Sraw * inv2),
-                                       sc.h3s * it.T, u0, it.delta, dr.x, dr.y, inv, sc.K);
-                else
+                unsigned char *rec = nullptr;
+                if (slot < B.ring_cap) {
+                    rec = B.ring + slot * B.rec_bytes;
+                    write_header(rec, it.idx, (uint32_t)p, 0u, sc.E0 * (dr.Sraw * inv2), sc.h3s * it.T, u0, it.delta);
+                } else {
                     atomicAdd(&W.cnt[2], 1u);
+                }
+                acc_draw_emit<KMAX, UNIF>(W.sig, W.act, ilo, ihi, sc.pid, k0, k1, inv, inv2, sc.K,
+                                          rec ? reinterpret_cast<float *>(rec + 32) : nullptr, W.spec);
             }
         }
 

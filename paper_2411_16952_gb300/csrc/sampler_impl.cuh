@@ -541,6 +541,63 @@ __device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long lo
     if (rec) write_record<KMAX>(rec, idx, point, 0u, sc.E0 * S, sc.h3s * T, u0, delta, dr.x, dr.y, inv, sc.K);
 }
 
+// Outputs of one accepted draw made again with rho_acc, in two passes so that
+// its 2K components are never all held: pass 1 sums |x|^2, S|x|^2 and
+// sum_k x_k (u(0) |x| / u0s) in mode order, pass 2 draws the modes again and
+// writes the projected state into the record (xh may be null: ring full) and
+// the spectrum terms.  The arithmetic and its order are those of draw_fast
+// and write_record / tally_spectrum, so the values are the same.
+struct DrawSums {
+    float nrm2, Sraw, u0raw;
+};
+template <int KMAX, bool UNIF>
+__device__ __forceinline__ DrawSums acc_draw_sums(const float *sig, const float *act, uint32_t lo, uint32_t hi,
+                                                  uint32_t pid, uint32_t k0, uint32_t k1) {
+    DrawSums d{0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int j = 0; j < (KMAX + 1) / 2; ++j) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, pid), k0, k1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * j + h;
+            if (m < KMAX) {
+                const float s = UNIF ? act[m] : sig[m];
+                float rho, xm, ym, rr;
+                box_muller_f32<true>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                const float sk = (s * s) * rho;
+                d.nrm2 += sk;
+                d.Sraw = fmaf((float)((m + 1) * (m + 1)), sk, d.Sraw);
+                d.u0raw += xm;
+            }
+        }
+    }
+    return d;
+}
+template <int KMAX, bool UNIF>
+__device__ __forceinline__ void acc_draw_emit(const float *sig, const float *act, uint32_t lo, uint32_t hi,
+                                              uint32_t pid, uint32_t k0, uint32_t k1, float inv, float inv2, int K,
+                                              float *xh, unsigned long long *s_spec) {
+    const float sc = inv2 * kSpecScale;
+#pragma unroll 1
+    for (int j = 0; j < (KMAX + 1) / 2; ++j) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, pid), k0, k1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = 2 * j + h;
+            if (m < K) {
+                const float s = UNIF ? act[m] : sig[m];
+                float rho, xm, ym, rr;
+                box_muller_f32<true>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                atomicAdd(&s_spec[m], (unsigned long long)__float2ull_rn(fmaf(xm, xm, ym * ym) * sc));
+                if (xh) {
+                    xh[m] = xm * inv;
+                    xh[K + m] = ym * inv;
+                }
+            }
+        }
+    }
+}
+
 // ---- the persistent sampler ----------------------------------------------
 // Floats between two threads' slabs of the accept hand-off (2 KMAX + 4: the
 // 16-byte pad moves consecutive lanes' vector stores to different banks).

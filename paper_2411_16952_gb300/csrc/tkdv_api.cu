@@ -155,6 +155,11 @@ int build_point(tkdv_sampler *h, int p, std::string &msg) {
 
 bool is_grid(const tkdv_sampler *h) { return h->launch.form == TKDV_H3_GRID_BF16X3; }
 
+// Threads per CTA of launch variant `variant` of the current form.
+int variant_threads(const tkdv_sampler *h, int variant) {
+    return is_grid(h) ? 128 * h->kg.nwg[variant] : kTriadVariantThreads[variant];
+}
+
 // Switch the form of the next runs (TKDV_H3_AUTO handles): its point table
 // and its default launch shape; the graph is rebuilt on the next run.
 int set_form(tkdv_sampler *h, int form) {
@@ -164,7 +169,7 @@ int set_form(tkdv_sampler *h, int form) {
     CK(cudaMemcpy(h->d_pts, h->pc.data(), sizeof(PointConst) * h->n_points, cudaMemcpyHostToDevice));
     if (form == TKDV_H3_GRID_BF16X3) {
         h->launch.variant = h->gfirst;
-        h->launch.threads = 128 * h->kg.nwg[h->gfirst];
+        h->launch.threads = variant_threads(h, h->gfirst);
     } else {
         h->launch.threads = 256;
         h->launch.variant = h->kmax == 128 ? 2 : 1;
@@ -196,10 +201,7 @@ int grid_tmem_cols(const tkdv_sampler *h, int variant) {
     return c;
 }
 
-// Threads per CTA of launch variant `variant` of the current form.
-int variant_threads(const tkdv_sampler *h, int variant) {
-    return is_grid(h) ? 128 * h->kg.nwg[variant] : kTriadVariantThreads[variant];
-}
+
 
 // Largest number of resident CTAs per SM for the handle's form.
 int max_ctas_per_sm(tkdv_sampler *h, int variant, int threads, int *out) {
@@ -542,7 +544,10 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
         h->gfirst = -1;
         for (int v = 0; v < h->kg.n_variants && e == cudaSuccess; ++v) {
             h->dyn_smem[v] = 2 * btile + (size_t)h->kg.nwg[v] * 2 * atile + 1024;
-            h->gvalid[v] = h->kg.nwg[v] * gridN <= 512 && h->dyn_smem[v] + 8192 <= (size_t)smem_optin;
+            cudaFuncAttributes fa{};
+            e = cudaFuncGetAttributes(&fa, h->kg.main[v][0]);
+            if (e != cudaSuccess) break;
+            h->gvalid[v] = h->kg.nwg[v] * gridN <= 512 && h->dyn_smem[v] + fa.sharedSizeBytes <= (size_t)smem_optin;
             if (!h->gvalid[v]) continue;
             if (h->gfirst < 0) h->gfirst = v;
             for (int u = 0; u < 2 && e == cudaSuccess; ++u) {
@@ -562,7 +567,7 @@ int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options
             return bail(TKDV_ERR_UNSUPPORTED);
         }
         h->launch.variant = h->gfirst;
-        h->launch.threads = 128 * h->kg.nwg[h->gfirst];
+        h->launch.threads = variant_threads(h, h->gfirst);
         std::vector<unsigned char> img(2 * btile);
         build_grid_image(h->K, h->kg.kmax, h->kg.ka, gridN, img.data());
         e = cudaMalloc(&h->d_bimg, img.size());

@@ -18,31 +18,33 @@ from . import (PROPOSAL_LEARNED, PROPOSAL_PAPER, Sampler, make_point, tkdv_log_M
                tkdv_mlp_step, tkdv_record_bytes)
 
 
-def collect_accepted(K, points, n_accept, seed=0, chunk=1 << 24, max_proposals=1 << 36, h3_mode=0, grid_N=0,
+def collect_accepted(K, points, n_accept, seed=0, pilot=1 << 20, max_proposals=1 << 36, h3_mode=0, grid_N=0,
                      stream=None):
     """Run the paper-proposal sampler on `points` [(beta', E0, C3/C2), ...] until
     every point has n_accept accepted records; returns (sampler, records
-    device buffer (torch uint8), record count, per-point alpha*, sigma^2)."""
+    device buffer (torch uint8), record count, per-point alpha*, sigma^2).
+    A pilot run measures each point's acceptance, and later runs give each
+    point the budget its remaining records need (30 % spare), so that points
+    of very different acceptance share one record ring of 2 n_accept records
+    per point without one crowding the others out."""
     import torch
     pts = [make_point(bp, E0, r, PROPOSAL_PAPER, point_id=p) for p, (bp, E0, r) in enumerate(points)]
     P = len(points)
-    S = Sampler(K, pts, h3_mode=h3_mode, grid_N=grid_N, sample_capacity=n_accept * P * 2, stream=stream)
-    budgets = np.full(P, chunk, dtype=np.uint64)
+    cap = n_accept * P * 2
+    S = Sampler(K, pts, h3_mode=h3_mode, grid_N=grid_N, sample_capacity=cap, stream=stream)
+    budgets = np.full(P, pilot, dtype=np.uint64)
     used = np.zeros(P, dtype=np.uint64)
     while True:
         S.run_budgets(budgets, seed)
         used += budgets
-        st = S.stats()
-        acc = np.array([s["n_accepted"] for s in st])
-        need = acc < n_accept
-        if not need.any() or used.max() >= max_proposals:
+        acc = np.array([s["n_accepted"] for s in S.stats()])
+        need = (acc < n_accept) & (used < max_proposals)
+        if not need.any():
             break
-        # remaining budget per point from its acceptance so far (at least one chunk)
         rate = np.maximum(acc, 1) / used.astype(np.float64)
-        budgets = np.where(need, np.minimum(np.maximum((n_accept - acc) / rate * 1.2, chunk), 1 << 32), 0)
-        budgets = budgets.astype(np.uint64)
+        want = np.ceil((n_accept - acc) * 1.3 / rate)
+        budgets = np.where(need, np.clip(want, pilot, min(1 << 32, max_proposals)), 0).astype(np.uint64)
     rb = tkdv_record_bytes(K)
-    cap = n_accept * P * 2
     buf = torch.empty(cap * rb, dtype=torch.uint8, device="cuda")
     n = S.samples(cap, device_dst=buf)
     info = [S.point_info(p) for p in range(P)]
@@ -50,10 +52,12 @@ def collect_accepted(K, points, n_accept, seed=0, chunk=1 << 24, max_proposals=1
 
 
 def train(K, points, n_accept=1 << 14, steps=300, lr=2e-2, tau=1.0, seed=0, sampler_seed=0, stream=None,
-          mlp=None):
+          mlp=None, h3_mode=0, grid_N=0):
     """Train the MLP on accepted samples of `points`; returns (mlp handle,
-    per-point corrections c (P x K), loss history)."""
-    S, buf, n, info = collect_accepted(K, points, n_accept, seed=sampler_seed, stream=stream)
+    per-point corrections c (P x K), loss history, training rows per point).
+    The samples come from the paper-proposal sampler in the given H3 form."""
+    S, buf, n, info = collect_accepted(K, points, n_accept, seed=sampler_seed, stream=stream, h3_mode=h3_mode,
+                                       grid_N=grid_N)
     P = len(points)
     feats = np.array([tkdv_mlp_features(K, bp, E0, r) for bp, E0, r in points])
     w_paper = [1.0 / np.asarray(s2) for (_, _, s2) in info]
@@ -68,6 +72,12 @@ def train(K, points, n_accept=1 << 14, steps=300, lr=2e-2, tau=1.0, seed=0, samp
     hist.append(tkdv_mlp_step(m, lr, tau, False))
     c = tkdv_mlp_infer(m, feats, [K] * P)[:, :K]
     return m, c, np.array(hist), tkdv_mlp_rows(m, P)
+
+
+def infer(mlp, K, points):
+    """Corrections c (P x K) of the trained network for points [(beta', E0, C3/C2), ...]."""
+    feats = np.array([tkdv_mlp_features(K, bp, E0, r) for bp, E0, r in points])
+    return tkdv_mlp_infer(mlp, feats, [K] * len(points))[:, :K]
 
 
 def learned_points(K, points, c, point_id0=0):

@@ -56,3 +56,18 @@ def speedup_k128(n=1 << 24):
     bps = np.geomspace(20.0, 60.0, 8)
     return dict(name="K128_speedup_8pts", K=128, E0=1.0, points=[(float(b), 9000.0 / float(b)) for b in bps],
                 n=n, seed=0)
+
+
+def pipeline_k64(lam_up=24000.0, r_scale=1.1):
+    """The 64-mode pipeline: K = 64, grid N = 256, E0 = 1.  Upstream ensemble at
+    beta' = 40 with beta' C3/C2 = 24000 (the paper has no K = 64 table; at
+    this K the skewness of u(0) reaches the 0.1 of the extreme K = 32 regime
+    near beta' C3/C2 = 27000, acceptance about 2e-5), 2^30 proposals.  The
+    downstream point has a stronger nonlinearity (C3/C2 times 1.1, the
+    shallower side of a depth change); its beta' is searched on [30, 50] by
+    bisection on the matching statistic, 16 candidates per step, 2^26
+    proposals each (2^30 per step), three steps."""
+    beta_up = 40.0
+    r_up = lam_up / beta_up
+    return dict(name="K64_pipeline", K=64, grid_N=256, E0=1.0, beta_up=beta_up, r_up=r_up, r_down=r_up * r_scale,
+                lo=30.0, hi=50.0, n_candidates=16, n_up=1 << 30, n_cand=1 << 26, steps=3, learn_accept=1 << 16)
