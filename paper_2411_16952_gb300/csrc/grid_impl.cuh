@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
     constexpr int KA = GS::KA, PART = GS::PART, KSTEPS = GS::KSTEPS, ATILE = GS::A_TILE;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ GridWG<KMAX> s_wg[NWG];
-    __shared__ __align__(8) unsigned long long s_mbar[NWG];
+    __shared__ __align__(8) unsigned long long s_mbar[NWG];  // the tile's products are in TMEM (MMA commit)
     __shared__ uint32_t s_tmem;
     __shared__ uint32_t s_abort;  // any warpgroup's device wait gave up: every warpgroup stops
 
@@ -359,6 +359,15 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 }
                 pending = true;
             }
+            // the terms of the decision that do not need the products, made
+            // while the tensor cores work: 1/|x|^2, S, ln Q, the accept word
+            const float inv2 = 1.f / nrm2;
+            const float inv = rsqrtf(nrm2);
+            const float S = Sraw * inv2;
+            const float tS = sc.cS * S;
+            const float tQ = UNIF ? 0.f : sc.cQ * logf(zz * inv2);
+            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
+            const float lnU = -0.5f * rho_fast(wa);
             // ---- 3. wait for the products, sum 2 C (C^2 + 3 S^2) of this row
             float cube = 0.f;
             bool ok = false;
@@ -411,16 +420,9 @@ __global__ void __launch_bounds__(128 * NWG, 1)
             }
             // ---- 4. decision
             const bool usable = valid && ok;
-            const float inv2 = 1.f / nrm2;
-            const float inv = rsqrtf(nrm2);
-            const float S = Sraw * inv2;
             const float T = cube * tscale * (inv2 * inv);
-            const float tS = sc.cS * S;
             const float tH = sc.cH * T;
-            const float tQ = UNIF ? 0.f : sc.cQ * logf(zz * inv2);
             const float delta = ((tS + tH) + tQ) - sc.logM;
-            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
-            const float lnU = -0.5f * rho_fast(wa);
             const float d = lnU - delta;
             const float guard = fmaf(
                 sc.ge * esum, inv,
