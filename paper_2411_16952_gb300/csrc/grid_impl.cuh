@@ -189,7 +189,7 @@ struct GridWG {
 
 // ---- the persistent grid-form sampler --------------------------------------
 // Dynamic shared memory (1024-byte aligned): [B hi | B lo | NWG x (A hi | A lo)].
-template <int KMAX, bool UNIF, int NWG>
+template <int KMAX, bool UNIF, int NWG, int UNR>
 __global__ void __launch_bounds__(128 * NWG, 1)
     k_sample_grid(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1,
                   const unsigned char *__restrict__ bimg, int gridN) {
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
             // cosine values to part 0 and sine values to part 1 of the row
             float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
             uint32_t wmin = 0xFFFFFFFFu;
-#pragma unroll(NWG >= 4 ? 1 : 2)
+#pragma unroll(UNR)
             for (int c8 = 0; c8 < KMAX / 8; ++c8) {
                 float vx[8], vy[8];
 #pragma unroll
@@ -569,11 +569,13 @@ void fill_grid_kernels_nwg(GridKernels *t, int variant, const void *g0, const vo
     t->ka = GridShape<KMAX>::KA;
 }
 
-// Variant v of the KMAX grid kernels with NWG warpgroups per CTA.
-template <int KMAX, int NWG>
+// Variant v of the KMAX grid kernels with NWG warpgroups per CTA; UNR groups
+// of eight modes in flight in the producer loop (measured best: 2 for four
+// warpgroups at 128 registers, 4 for three at 168).
+template <int KMAX, int NWG, int UNR = (NWG == 3 ? 4 : 2)>
 void fill_grid_variant(GridKernels *t, int variant) {
-    fill_grid_kernels_nwg<KMAX>(t, variant, (const void *)k_sample_grid<KMAX, false, NWG>,
-                                (const void *)k_sample_grid<KMAX, true, NWG>, NWG);
+    fill_grid_kernels_nwg<KMAX>(t, variant, (const void *)k_sample_grid<KMAX, false, NWG, UNR>,
+                                (const void *)k_sample_grid<KMAX, true, NWG, UNR>, NWG);
 }
 
 }  // namespace tkdv
