@@ -73,9 +73,13 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (None, "not captured since the kernel last changed"),
+    "grid": (127232.0 / (8 * 4194304),
+             "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,2>, 8 x 2^22 proposals)"),
     "triad": (None, "not captured since the kernel last changed"),
 }
+# the 64-mode grid kernel: one capture of the upstream run at 2^26 proposals
+TRAFFIC_PER_PROPOSAL_K64 = ((187648.0 + 256.0) / (1 << 26),
+                            "ncu --set full capture prof_grid_k64 (k_sample_grid<64,0,2,2>, 2^26 proposals)")
 
 
 def alu_peak(n_sms, peaks):
@@ -310,7 +314,7 @@ def train_learned(T, K, pts3, grid_N, n_accept, steps, tau, seed, stream, keep=F
                   "points": info}, mlp
 
 
-def k64_pipeline(T, args, stream, peaks, n_sms, rank):
+def k64_pipeline(T, args, stream, peaks, n_sms, rank, learned=True, shift=0):
     """The 64-mode pipeline (learned proposal + BF16 hi/lo grid form, N = 256):
     the upstream ensemble (2^30 proposals, one run), then the downstream beta'
     by bisection on the matching statistic (here the ensemble mean of
@@ -323,11 +327,19 @@ def k64_pipeline(T, args, stream, peaks, n_sms, rank):
     from paper_2411_16952_gb300 import workloads
     import torch
     pw = workloads.pipeline_k64()
+    pw["n_up"] >>= shift
+    pw["n_cand"] >>= shift
     K, N, E0 = pw["K"], pw["grid_N"], pw["E0"]
     up = (pw["beta_up"], E0, pw["r_up"])
     train_pts = [up] + [(float(b), E0, pw["r_down"]) for b in np.linspace(pw["lo"], pw["hi"], 7)]
-    corr, info, mlp = train_learned(T, K, train_pts, N, pw["learn_accept"], args.learn_steps, args.learn_tau,
-                                    rank + 3000, stream, keep=True)
+    if learned:
+        corr, info, mlp = train_learned(T, K, train_pts, N, pw["learn_accept"], args.learn_steps, args.learn_tau,
+                                        rank + 3000, stream, keep=True)
+    else:  # the paper's Sigma throughout (c = 0)
+        corr = np.zeros((len(train_pts), K))
+        info = {"train_seconds": 0.0, "tau": None, "accepted_rows_per_point": [],
+                "points": [{"gain": 1.0, "fallback_to_paper": True} for _ in train_pts]}
+        mlp = None
     runs = []
 
     def timed_run(points, budget, seed):
@@ -355,7 +367,7 @@ def k64_pipeline(T, args, stream, peaks, n_sms, rank):
 
         def run_batch(betas, pid0, n, seed):
             pts3 = [(float(b), E0, pw["r_down"]) for b in betas]
-            c = L.infer(mlp, K, pts3)
+            c = L.infer(mlp, K, pts3) if mlp is not None else np.zeros((len(pts3), K))
             points = [T.make_point(b, e, r, T.PROPOSAL_LEARNED, point_id=rank * 4096 + 1 + pid0 + j,
                                    log_var_correction=c[j]) for j, (b, e, r) in enumerate(pts3)]
             return timed_run(points, n, seed)
@@ -367,7 +379,8 @@ def k64_pipeline(T, args, stream, peaks, n_sms, rank):
     except (ValueError, T.TkdvError) as e:  # the statistic did not bracket the target, or a run failed
         res, err = None, str(e)
     finally:
-        L.close(mlp)
+        if mlp is not None:
+            L.close(mlp)
     t_s = sum(r["ms"] for r in runs) / 1e3
     props = sum(r["proposals"] for r in runs)
     acc = sum(r["accepted"] for r in runs)
@@ -375,7 +388,9 @@ def k64_pipeline(T, args, stream, peaks, n_sms, rank):
     ops = alg_ops_per_proposal(K, "grid", N)
     tf = tensor_flops_per_proposal(K, N) * pps / 1e12
     tpk = float(peaks.get("bf16_tflops_sustained", 1735.3))
-    out = {"workload": pw["name"], "K": K, "grid_N": N, "form": "grid_bf16x3_learned", "error": err,
+    out = {"workload": pw["name"], "K": K, "grid_N": N, "error": err,
+           "traffic_per_proposal": TRAFFIC_PER_PROPOSAL_K64[0], "traffic_source": TRAFFIC_PER_PROPOSAL_K64[1],
+           "form": "grid_bf16x3_learned" if learned else "grid_bf16x3_paper",
            "proposals_per_s": pps, "accepted_per_s": acc / t_s if t_s > 0 else 0.0, "runs": runs,
            "roofline": {"alu": {"ops_per_proposal": ops, "achieved": ops * pps / 1e12, "peak": alu_peak(n_sms, peaks),
                                 "unit": "Tops/s", "frac": ops * pps / 1e12 / alu_peak(n_sms, peaks)},
@@ -455,6 +470,11 @@ def main():
     ap.add_argument("--batch-learn-accept", type=int, default=1 << 14,
                     help="64-point batch: accepted samples per point to train its network on")
     ap.add_argument("--no-k64", action="store_true", help="skip the 64-mode pipeline")
+    ap.add_argument("--only-k64", action="store_true",
+                    help="run only the 64-mode pipeline (with --k64-paper: the paper's Sigma, no training) and "
+                         "print its JSON object")
+    ap.add_argument("--k64-paper", action="store_true")
+    ap.add_argument("--k64-shift", type=int, default=0, help="64-mode pipeline: proposals divided by 2^shift")
     ap.add_argument("--no-k128", action="store_true", help="skip the K = 128 measurement")
     ap.add_argument("--k128-n", type=int, default=1 << 24, help="K = 128: proposals per point and step")
     args = ap.parse_args()
@@ -478,6 +498,10 @@ def main():
     K, E0, n, gN = wl["K"], wl["E0"], args.n_per_point, wl["grid_N"]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    if args.only_k64:
+        print(json.dumps({"k64_pipeline": k64_pipeline(T, args, stream, peaks, n_sms, rank,
+                                                       learned=not args.k64_paper, shift=args.k64_shift)}))
+        return
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     import datetime as dt
     clk = Clocks(local)  # started before any warm-up so that its start-up stays out of the timed steps
@@ -682,7 +706,7 @@ def main():
     # the 64-mode pipeline (learned + grid form, bisection of the downstream beta')
     k64 = None
     if not args.no_k64 and ws == 1 and "grid_bf16x3_learned" in forms:
-        k64 = k64_pipeline(T, args, stream, peaks, n_sms, rank)
+        k64 = k64_pipeline(T, args, stream, peaks, n_sms, rank, shift=args.k64_shift)
 
     h = results[headline]
     form_kind = "grid" if headline.startswith("grid") else "triad"
