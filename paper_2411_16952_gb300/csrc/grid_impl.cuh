@@ -187,8 +187,19 @@ struct GridWG {
     float sig[KMAX], act[KMAX];
 };
 
+// One row of a tile between its draw and its decision.
+struct GridRow {
+    unsigned long long idx;
+    float nrm2, Sraw, zz, esum;
+    bool valid;
+    bool tail;  // a radius word in the lowest bucket of the uniform map
+};
+
 // ---- the persistent grid-form sampler --------------------------------------
 // Dynamic shared memory (1024-byte aligned): [B hi | B lo | NWG x (A hi | A lo)].
+// (A second A tile per warpgroup, drawing tile t+1 before waiting for the
+// products of tile t, measured 8 % slower at three warpgroups than one tile
+// with the product-free decision terms made before the wait.)
 template <int KMAX, bool UNIF, int NWG, int UNR>
 __global__ void __launch_bounds__(128 * NWG, 1)
     k_sample_grid(const __grid_constant__ DevBufs B, const __grid_constant__ RunArgs A, uint32_t k0, uint32_t k1,
@@ -288,77 +299,13 @@ __global__ void __launch_bounds__(128 * NWG, 1)
         float maxd = -INFINITY;
         uint32_t nacc = 0;  // accepted draws of this warp in this chunk (the same in every lane)
 
-        for (uint32_t i0 = 0; i0 < n_here; i0 += 128) {
-            const uint32_t i = i0 + (uint32_t)t;
-            const bool valid = i < n_here;
-            const unsigned long long idx = cbase + i;
+        const uint32_t n_tiles = (n_here + 127u) / 128u;
+        // ---- 3./4. the products and the decision of one row
+        auto consume = [&](const GridRow &r) {
+            const unsigned long long idx = r.idx;
             const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
-            // ---- 1. the row of X: eight modes (four Philox blocks) at a time,
-            // cosine values to part 0 and sine values to part 1 of the row
-            float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
-            uint32_t wmin = 0xFFFFFFFFu;
-#pragma unroll(UNR)
-            for (int c8 = 0; c8 < KMAX / 8; ++c8) {
-                float vx[8], vy[8];
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int j = 4 * c8 + jj;
-                    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk.k);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int m = 2 * j + h;
-                        const float act = W.act[m];  // 1 for modes up to K, else 0
-                        const float s = UNIF ? act : W.sig[m];
-                        float rho, xm, ym, rr;
-                        box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
-                        wmin = min(wmin, h ? w.z : w.x);
-                        esum = fmaf(s, rr, esum);
-                        vx[2 * jj + h] = xm;
-                        vy[2 * jj + h] = ym;
-                        const float sk = (s * s) * rho;
-                        nrm2 += sk;
-                        Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
-                        zz = fmaf(act, rho, zz);  // the active modes' squared radii
-                    }
-                }
-                uint4 hx, lx, hy, ly;
-                split8(vx, hx, lx);
-                split8(vy, hy, ly);
-                const uint32_t ox = sw128_offset((uint32_t)t, (uint32_t)(8 * c8), 128u);
-                const uint32_t oy = sw128_offset((uint32_t)t, (uint32_t)(PART + 8 * c8), 128u);
-                *reinterpret_cast<uint4 *>(ga_hi + ox) = hx;
-                *reinterpret_cast<uint4 *>(ga_lo + ox) = lx;
-                *reinterpret_cast<uint4 *>(ga_hi + oy) = hy;
-                *reinterpret_cast<uint4 *>(ga_lo + oy) = ly;
-            }
-            const bool tail_r = wmin < kTailBucket;
-            fence_async_smem();
-            wg_sync(g);
-            // ---- 2. one thread issues the contraction of the tile
-            const bool run_mma = W.abort == 0;
-            if (run_mma) {
-                if (t == 0) {
-                    tc_fence_after();
-#pragma unroll
-                    for (int part = 0; part < 2; ++part) {
-                        const uint32_t dt = part ? tmem_s : tmem_c;
-#pragma unroll
-                        for (int ks = 0; ks < KSTEPS; ++ks) {
-                            const uint32_t kcol = (uint32_t)(part * PART + 16 * ks);
-                            const uint32_t koff = (kcol & 63u) * 2u;  // bytes into the swizzle atom
-                            const uint32_t aat = (kcol >> 6) * 128u * 128u;
-                            const uint32_t bat = (kcol >> 6) * (uint32_t)half * 128u;
-                            const uint64_t dah = sw128_desc(a_hi + aat + koff), dal = sw128_desc(a_lo + aat + koff);
-                            const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
-                            umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                            umma_bf16(dt, dah, dbl, idesc, 1u);
-                            umma_bf16(dt, dal, dbh, idesc, 1u);
-                        }
-                    }
-                    umma_commit(mbar);
-                }
-                pending = true;
-            }
+            const bool valid = r.valid, tail_r = r.tail;
+            const float nrm2 = r.nrm2, Sraw = r.Sraw, zz = r.zz, esum = r.esum;
             // the terms of the decision that do not need the products, made
             // while the tensor cores work: 1/|x|^2, S, ln Q, the accept word
             const float inv2 = 1.f / nrm2;
@@ -472,6 +419,88 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 }
                 nacc += (uint32_t)__popc(ma);
             }
+        };
+        for (uint32_t trip = 0; trip < n_tiles; ++trip) {
+            GridRow cur;
+            {  // ---- 1. this thread's row of the tile
+                const uint32_t i = trip * 128u + (uint32_t)t;
+                const unsigned long long idx = cbase + i;
+                const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
+                // ---- 1. the row of X: eight modes (four Philox blocks) at a time,
+                // cosine values to part 0 and sine values to part 1 of the row
+                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
+                uint32_t wmin = 0xFFFFFFFFu;
+#pragma unroll(UNR)
+                for (int c8 = 0; c8 < KMAX / 8; ++c8) {
+                    float vx[8], vy[8];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * c8 + jj;
+                        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk.k);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int m = 2 * j + h;
+                            const float act = W.act[m];  // 1 for modes up to K, else 0
+                            const float s = UNIF ? act : W.sig[m];
+                            float rho, xm, ym, rr;
+                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                            wmin = min(wmin, h ? w.z : w.x);
+                            esum = fmaf(s, rr, esum);
+                            vx[2 * jj + h] = xm;
+                            vy[2 * jj + h] = ym;
+                            const float sk = (s * s) * rho;
+                            nrm2 += sk;
+                            Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
+                            zz = fmaf(act, rho, zz);  // the active modes' squared radii
+                        }
+                    }
+                    uint4 hx, lx, hy, ly;
+                    split8(vx, hx, lx);
+                    split8(vy, hy, ly);
+                    const uint32_t ox = sw128_offset((uint32_t)t, (uint32_t)(8 * c8), 128u);
+                    const uint32_t oy = sw128_offset((uint32_t)t, (uint32_t)(PART + 8 * c8), 128u);
+                    *reinterpret_cast<uint4 *>(ga_hi + ox) = hx;
+                    *reinterpret_cast<uint4 *>(ga_lo + ox) = lx;
+                    *reinterpret_cast<uint4 *>(ga_hi + oy) = hy;
+                    *reinterpret_cast<uint4 *>(ga_lo + oy) = ly;
+                }
+                cur.idx = idx;
+                cur.valid = i < n_here;
+                cur.nrm2 = nrm2;
+                cur.Sraw = Sraw;
+                cur.zz = zz;
+                cur.esum = esum;
+                cur.tail = wmin < kTailBucket;
+            }
+            {  // ---- 2. after the warpgroup barrier one thread issues the contraction of the tile
+                fence_async_smem();
+                wg_sync(g);
+                const bool run_mma = W.abort == 0;
+                if (run_mma) {
+                    if (t == 0) {
+                        tc_fence_after();
+#pragma unroll
+                        for (int part = 0; part < 2; ++part) {
+                            const uint32_t dt = part ? tmem_s : tmem_c;
+#pragma unroll
+                            for (int ks = 0; ks < KSTEPS; ++ks) {
+                                const uint32_t kcol = (uint32_t)(part * PART + 16 * ks);
+                                const uint32_t koff = (kcol & 63u) * 2u;  // bytes into the swizzle atom
+                                const uint32_t aat = (kcol >> 6) * 128u * 128u;
+                                const uint32_t bat = (kcol >> 6) * (uint32_t)half * 128u;
+                                const uint64_t dah = sw128_desc(a_hi + aat + koff), dal = sw128_desc(a_lo + aat + koff);
+                                const uint64_t dbh = sw128_desc(b_hi + bat + koff), dbl = sw128_desc(b_lo + bat + koff);
+                                umma_bf16(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                                umma_bf16(dt, dah, dbl, idesc, 1u);
+                                umma_bf16(dt, dal, dbh, idesc, 1u);
+                            }
+                        }
+                        umma_commit(mbar);
+                    }
+                    pending = true;
+                }
+            }
+            consume(cur);
         }
 
         // ---- outputs of this warp's accepted draws of the chunk, 32 at a time:

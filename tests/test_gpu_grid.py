@@ -153,7 +153,8 @@ def test_grid_rejects_bad_grids(T):
 @pytest.mark.parametrize("K,N,bp,r", [(16, 64, 20.0, 75.0), (32, 128, 40.0, 75.0), (64, 256, 40.0, 225.0)])
 def test_every_grid_launch_variant_gives_the_same_results(T, K, N, bp, r):
     """Each launch variant of the grid form that fits (two, three or four
-    warpgroups sharing the basis) gives the same statistics and the same records, at an
+    warpgroups sharing the basis) gives the same statistics and the same
+    records, at an
     acceptance where most tiles hold accepted draws and on two points, so
     that the outputs of accepted draws and the change of point are exercised."""
     lm = T.tkdv_log_M(K, bp, 1.0, r, np.array(O.make_point(K, 1.0, bp, r, O.PAPER).sigma2[:K])) - 2.5
