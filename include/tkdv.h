@@ -86,9 +86,9 @@ int tkdv_check_radius_error_log(double *max_ratio, uint32_t *worst_word);
 #define TKDV_H3_TRIAD_F32 0   /* double sum of Eq. (42) on FP32 CUDA cores */
 #define TKDV_H3_GRID_BF16X3 1 /* grid cubature of Eq. (2) as a tensor-core contraction, BF16 hi/lo x3 */
 #define TKDV_H3_AUTO 2        /* the library chooses: the grid form where it exists (sm_10x device, K <= 64,
-                                 not SIR), else the triad form; sampler_autotune then times both and keeps
-                                 the faster (the triad form wins at acceptances above about 0.1, where the
-                                 grid form's per-accept redraw weighs more); sampler_h3_form tells which */
+                                 not SIR), else the triad form; sampler_autotune then times both forms
+                                 and all their launch shapes and keeps the fastest; sampler_h3_form
+                                 tells which */
 
 #define TKDV_MAX_POINTS 64
 #define TKDV_HIST_BINS 256
@@ -200,9 +200,12 @@ int sampler_create(int K, double beta_p, double E0, double r, int proposal, tkdv
 /* sampler_create_ex: n_points (1..64) points sharing opt->K and opt->h3_mode,
    run together by one persistent launch (batched form).  Errors as above,
    plus UNSUPPORTED for the grid form on a device without tcgen05.  The grid
-   form runs K <= 16 with two 128-proposal tiles per CTA and K <= 32 and
-   K <= 64 with one (shared memory: 2 x grid_N x 2K x 2 B basis plus
-   2 x 128 x 2K x 2 B per tile). */
+   form keeps one copy of the mirror-pair basis per CTA (grid_N/2 rows x KA
+   columns, KA = 2 x the mode bound 16, 32 or 64, BF16 hi and lo) and two to
+   four warpgroups, each with its own 128-proposal A tile (128 x KA, hi and
+   lo) and grid_N TMEM columns; a launch shape is offered only where its
+   warpgroups x grid_N <= 512 TMEM columns and its tiles fit the shared
+   memory. */
 int sampler_create_ex(const tkdv_point *points, int n_points, const tkdv_options *opt,
                       tkdv_sampler **out);
 
@@ -301,8 +304,10 @@ int sampler_batch_run(const tkdv_point *points, int n_points, const tkdv_options
    default or autotuned one.  variant: triad form 0 = 128 threads, 1 = 256
    threads, 2 = 256 threads held to 128 registers (two CTAs per SM), 3..5 the
    same with the per-lane accept path (for K > 64: 0..2 of the warp form; SIR
-   runs: 1; grid form: 0).  ctas_per_sm: 1 .. the occupancy maximum of that
-   variant, 0 for the maximum.  Results do not depend on the launch shape.
+   runs: 1; grid form, by mode bound: K <= 16: 0 = four warpgroups per CTA,
+   1 = two; 16 < K <= 32: 0 = four, 1 = three, 2 = two; 32 < K <= 64: 0 = two;
+   each offered where it fits, see sampler_create_ex).  ctas_per_sm: 1 .. the
+   occupancy maximum of that variant, 0 for the maximum.  Results do not depend on the launch shape.
    Errors: INVALID_ARG (no such variant for the handle's form, ctas_per_sm
    above the maximum), CUDA. */
 int sampler_set_launch(tkdv_sampler *h, int variant, int ctas_per_sm);
