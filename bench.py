@@ -73,12 +73,12 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (127232.0 / (8 * 4194304),
-             "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,2>, 8 x 2^22 proposals)"),
+    "grid": (130304.0 / (8 * 4194304),
+             "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,4>, 8 x 2^22 proposals)"),
     "triad": (None, "not captured since the kernel last changed"),
 }
 # the 64-mode grid kernel: one capture of the upstream run at 2^26 proposals
-TRAFFIC_PER_PROPOSAL_K64 = ((187648.0 + 256.0) / (1 << 26),
+TRAFFIC_PER_PROPOSAL_K64 = (202752.0 / (1 << 26),
                             "ncu --set full capture prof_grid_k64 (k_sample_grid<64,0,2,2>, 2^26 proposals)")
 
 

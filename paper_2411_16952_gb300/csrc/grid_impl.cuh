@@ -308,12 +308,12 @@ __global__ void __launch_bounds__(128 * NWG, 1)
             const float nrm2 = r.nrm2, Sraw = r.Sraw, zz = r.zz, esum = r.esum;
             // the terms of the decision that do not need the products, made
             // while the tensor cores work: 1/|x|^2, S, ln Q, the accept word
-            const float inv2 = 1.f / nrm2;
-            const float inv = rsqrtf(nrm2);
+            const float inv2 = rcp_rn(nrm2);
+            const float inv = rsqrt_approx(nrm2);
             const float S = Sraw * inv2;
             const float tS = sc.cS * S;
             const float tQ = UNIF ? 0.f : sc.cQ * logf(zz * inv2);
-            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
+            const uint32_t wa = PhiloxRow(lo, hi, sc.pid, A.rk.k).block((uint32_t)((sc.K + 1) / 2)).x;
             const float lnU = -0.5f * rho_fast(wa);
             // ---- 3. wait for the products, sum 2 C (C^2 + 3 S^2) of this row
             float cube = 0.f;
@@ -430,13 +430,14 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 // cosine values to part 0 and sine values to part 1 of the row
                 float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
                 uint32_t wmin = 0xFFFFFFFFu;
+                const PhiloxRow prow(lo, hi, sc.pid, A.rk.k);
 #pragma unroll(UNR)
                 for (int c8 = 0; c8 < KMAX / 8; ++c8) {
                     float vx[8], vy[8];
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = 4 * c8 + jj;
-                        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)j, lo, hi, sc.pid), A.rk.k);
+                        const uint4 w = prow.block((uint32_t)j);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int m = 2 * j + h;
@@ -518,8 +519,8 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 const AcceptItem it = slab[b0 + lane];
                 const uint32_t ilo = (uint32_t)it.idx, ihi = (uint32_t)(it.idx >> 32);
                 const DrawSums dr = acc_draw_sums<KMAX, UNIF>(W.sig, W.act, ilo, ihi, sc.pid, k0, k1);
-                const float inv2 = 1.f / dr.nrm2;
-                const float inv = rsqrtf(dr.nrm2);
+                const float inv2 = rcp_rn(dr.nrm2);
+                const float inv = rsqrt_approx(dr.nrm2);
                 const float u0 = sc.u0s * dr.u0raw * inv;
                 atomicAdd(&W.hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
                 atomicAdd(&W.exc[exc_bin(u0, sc.ea)], 1u);
@@ -598,10 +599,12 @@ void fill_grid_kernels_nwg(GridKernels *t, int variant, const void *g0, const vo
     t->ka = GridShape<KMAX>::KA;
 }
 
-// Variant v of the KMAX grid kernels with NWG warpgroups per CTA; UNR groups
-// of eight modes in flight in the producer loop (measured best: 2 for four
-// warpgroups at 128 registers, 4 for three at 168).
-template <int KMAX, int NWG, int UNR = (NWG == 3 ? 4 : 2)>
+// Variant v of the KMAX grid kernels with NWG warpgroups per CTA; the
+// producer loop over groups of eight modes unrolled UNR times (measured at 32
+// modes: 4, the whole loop, for four and three warpgroups, 11.34e9 against
+// 11.00e9 proposals/s with 2 at four; 2 for two warpgroups, at 32 and at 64
+// modes, where 4 measured 2 % and 5 % slower).
+template <int KMAX, int NWG, int UNR = (NWG >= 3 ? 4 : 2)>
 void fill_grid_variant(GridKernels *t, int variant) {
     fill_grid_kernels_nwg<KMAX>(t, variant, (const void *)k_sample_grid<KMAX, false, NWG, UNR>,
                                 (const void *)k_sample_grid<KMAX, true, NWG, UNR>, NWG);

@@ -46,9 +46,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // The same block with the round keys given (RoundKeys: round r uses
 // rk[2r], rk[2r+1]); rk points at the run's kernel arguments, so every key is
-// a constant operand of its round.
-// Each round's two products are formed as full 64-bit products (one wide
-// multiply each, high and low words together).
+// a constant operand of its round.  Each round's two products are formed as
+// full 64-bit products (one wide multiply each, high and low words together).
 __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -59,6 +58,17 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk) {
     }
     return c;
 }
+// The blocks (j, lo, hi, pid), j = 0, 1, ..., of one proposal from the round
+// keys.  (Making the two products that do not depend on j, M1 hi in round 1
+// and M0 (hi(M1 hi) ^ lo ^ rk[0]) in round 2, once per proposal measured
+// no faster: 10.91e9 against 10.98e9 proposals/s at K = 32.)
+struct PhiloxRow {
+    const uint32_t *rk;
+    uint32_t lo, hi, pid;
+    __device__ __forceinline__ PhiloxRow(uint32_t lo_, uint32_t hi_, uint32_t pid_, const uint32_t *rk_)
+        : rk(rk_), lo(lo_), hi(hi_), pid(pid_) {}
+    __device__ __forceinline__ uint4 block(uint32_t j) const { return philox4x32_10_rk(make_uint4(j, lo, hi, pid), rk); }
+};
 
 // (2 floor(w/512) + 1) 2^-24, exact in FP32: the float 1 + m 2^-23 with
 // m = w >> 9 is built from its bits, and subtracting 1 - 2^-24 (a float) is
@@ -105,6 +115,34 @@ __device__ __forceinline__ float angle_f(uint32_t w) {
     return fmaf(k2Pi, __uint_as_float(0x3f800000u | (w >> 9)) - 1.5f, k2Pi * 0x1p-24f);
 }
 
+// The hardware approximations of PTX (lg2, rsqrt, sin, cos .approx) in their
+// flush-to-zero forms.  Every argument the sampler gives them (u in
+// [2^-24, 1), rho >= 2^-25, |x|^2 > 0, angles of magnitude >= 2 pi 2^-24) and
+// every result is a normal float, where the flushing forms return the same
+// documented approximation without handling for subnormal operands.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// 1/x correctly rounded (the value of 1.f / x) for normal x and 1/x: the
+// flushing form of the rounded reciprocal, without the subnormal path of the
+// division.
+__device__ __forceinline__ float rcp_rn(float x) {
+    float y;
+    asm("rcp.rn.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_approx(float a, float &sn, float &cs) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(a));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(a));
+}
+
 // Squared Box-Muller radius rho = -2 ln u for u = u01f(w), FP32.
 // rho_fast (the decision path) takes the hardware base-2 logarithm, whose
 // documented error is at most 2 ulp below 1/2 and 2^-22 absolute on [1/2, 2):
@@ -113,7 +151,7 @@ __device__ __forceinline__ float angle_f(uint32_t w) {
 // part per draw from sum_m sigma_m / sqrt(rho_m).  The floor keeps rho
 // positive where that error could cross zero.
 __device__ __forceinline__ float rho_fast(uint32_t w) {
-    return fmaxf(__log2f(u01f(w)) * -1.38629436111989061883f, 0x1p-25f);
+    return fmaxf(lg2_approx(u01f(w)) * -1.38629436111989061883f, 0x1p-25f);
 }
 // rho_acc (the outputs of accepted draws) is rho_fast below u = 1 - 2^-9
 // (there rho >= 2^-8 and the absolute error is a small relative one) and
@@ -149,10 +187,10 @@ template <bool ACC>
 __device__ __forceinline__ void box_muller_f32(uint32_t w1, uint32_t w2, float s, float &rho, float &x, float &y,
                                                float &rr) {
     rho = ACC ? rho_acc(w1) : rho_fast(w1);
-    rr = rsqrtf(rho);
+    rr = rsqrt_approx(rho);
     const float a = (-s * rho) * rr;
     float sn, cs;
-    __sincosf(angle_f(w2), &sn, &cs);
+    sincos_approx(angle_f(w2), sn, cs);
     x = a * cs;
     y = a * sn;
 }
@@ -213,32 +251,26 @@ struct Draw {
     float rrmax;    // largest sigma_m/sqrt(rho_m): above kOutputRr |x| outputs need rho_acc
 };
 
-// Philox keys: the key pair (key schedule computed per block) or the run's
-// round keys.
-struct KeyPair {
-    uint32_t k0, k1;
-    __device__ __forceinline__ uint4 block(uint4 c) const { return philox4x32_10(c, k0, k1); }
-};
-struct KeyRounds {
-    const uint32_t *rk;
-    __device__ __forceinline__ uint4 block(uint4 c) const { return philox4x32_10_rk(c, rk); }
+// The blocks of one proposal: from the key pair (key schedule computed per
+// block), or PhiloxRow from the run's round keys.
+struct PairRow {
+    uint32_t lo, hi, pid, k0, k1;
+    __device__ __forceinline__ uint4 block(uint32_t j) const { return philox4x32_10(make_uint4(j, lo, hi, pid), k0, k1); }
 };
 
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
-template <int KMAX, bool UNIF, bool ACC = false, typename Keys = KeyPair>
-__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act,
-                                            uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, Keys keys);
+template <int KMAX, bool UNIF, bool ACC = false, typename Row = PairRow>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act, const Row &row);
 
 template <int KMAX, bool UNIF, bool ACC = false>
 __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
                                           uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                           uint32_t k0, uint32_t k1) {
-    draw_fast_k<KMAX, UNIF, ACC>(d, sig, act, idx_lo, idx_hi, pid, KeyPair{k0, k1});
+    draw_fast_k<KMAX, UNIF, ACC>(d, sig, act, PairRow{idx_lo, idx_hi, pid, k0, k1});
 }
 
-template <int KMAX, bool UNIF, bool ACC, typename Keys>
-__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act,
-                                            uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, Keys keys) {
+template <int KMAX, bool UNIF, bool ACC, typename Row>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act, const Row &row) {
     d.nrm2 = 0.f;
     d.Sraw = 0.f;
     d.zz = 0.f;
@@ -248,7 +280,7 @@ __device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, con
     d.rrmax = 0.f;
 #pragma unroll
     for (int j = 0; j < (KMAX + 1) / 2; ++j) {
-        const uint4 w = keys.block(make_uint4((uint32_t)j, idx_lo, idx_hi, pid));
+        const uint4 w = row.block((uint32_t)j);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
@@ -347,8 +379,8 @@ struct Fast {
 template <int KMAX, bool UNIF>
 __device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, uint32_t wacc) {
     Fast f;
-    const float inv2 = 1.f / dr.nrm2;
-    f.inv = rsqrtf(dr.nrm2);
+    const float inv2 = rcp_rn(dr.nrm2);
+    f.inv = rsqrt_approx(dr.nrm2);
     f.S = dr.Sraw * inv2;
     f.T = triad2<KMAX>(dr.x, dr.y) * (inv2 * f.inv);
     const float tS = c.cS * f.S;
@@ -365,10 +397,6 @@ __device__ __forceinline__ Fast eval_fast(const Draw<KMAX> &dr, const Scal &c, u
 __device__ __forceinline__ uint32_t accept_word(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                                 int K, uint32_t k0, uint32_t k1) {
     return philox4x32_10(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), k0, k1).x;
-}
-__device__ __forceinline__ uint32_t accept_word_rk(uint32_t idx_lo, uint32_t idx_hi, uint32_t pid, int K,
-                                                   const uint32_t *rk) {
-    return philox4x32_10_rk(make_uint4((uint32_t)((K + 1) / 2), idx_lo, idx_hi, pid), rk).x;
 }
 
 __device__ __forceinline__ int hist_bin(float u0, float a, float b) {
@@ -530,8 +558,8 @@ __device__ __noinline__ void emit_accepted(const PointConst *P, unsigned long lo
     const Scal sc = load_scal(P);
     Draw<KMAX> dr;
     draw_fast<KMAX, UNIF, true>(dr, sig, act, (uint32_t)idx, (uint32_t)(idx >> 32), sc.pid, k0, k1);
-    const float inv2 = 1.f / dr.nrm2;
-    const float inv = rsqrtf(dr.nrm2);
+    const float inv2 = rcp_rn(dr.nrm2);
+    const float inv = rsqrt_approx(dr.nrm2);
     const float S = dr.Sraw * inv2;
     const float T = triad2<KMAX>(dr.x, dr.y) * (inv2 * inv);
     const float tQ = UNIF ? 0.f : sc.cQ * logf(dr.zz * inv2);
@@ -674,8 +702,9 @@ __global__ void __launch_bounds__(NT, MINB)
             const unsigned long long idx = base + i;
             const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
             Draw<KMAX> dr;
-            draw_fast_k<KMAX, UNIF>(dr, s_sig, s_act, lo, hi, sc.pid, KeyRounds{A.rk.k});
-            const uint32_t wa = accept_word_rk(lo, hi, sc.pid, sc.K, A.rk.k);
+            const PhiloxRow prow(lo, hi, sc.pid, A.rk.k);
+            draw_fast_k<KMAX, UNIF>(dr, s_sig, s_act, prow);
+            const uint32_t wa = prow.block((uint32_t)((sc.K + 1) / 2)).x;
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
             // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
             const bool tail = min(dr.wmin, wa) < kTailBucket;
@@ -1022,8 +1051,8 @@ __global__ void __launch_bounds__(128) k_replay(const PointConst *P, const unsig
         // the sampler's outputs of an accepted draw would be
         draw_fast<KMAX, UNIF, true>(dr, P->sigma, P->act, lo, hi, sc.pid, k0, k1);
     }
-    const float inv2 = 1.f / dr.nrm2;
-    const float inv = rsqrtf(dr.nrm2);
+    const float inv2 = rcp_rn(dr.nrm2);
+    const float inv = rsqrt_approx(dr.nrm2);
     const float S = dr.Sraw * inv2;
     const float T = triad2<KMAX>(dr.x, dr.y) * (inv2 * inv);
     const float tQ = UNIF ? 0.f : sc.cQ * logf(dr.zz * inv2);

@@ -147,9 +147,9 @@ __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, cons
                 const int m = 2 * j + h;
                 const float s = UNIF ? act[m] : sig[m];
                 const float rho = rho_log(h ? w.z : w.x);
-                const float a = (-s * rho) * rsqrtf(rho);
+                const float a = (-s * rho) * rsqrt_approx(rho);
                 float sn, cs;
-                __sincosf(angle_f(h ? w.w : w.y), &sn, &cs);
+                sincos_approx(angle_f(h ? w.w : w.y), sn, cs);
                 const float xm = a * cs, ym = a * sn;
                 if (m < K) wmin[q] = min(wmin[q], h ? w.z : w.x);
                 sv[q * kWS + wpos(m)] = make_float2(xm, ym);
@@ -197,8 +197,8 @@ __device__ __forceinline__ WEval warp_batch(float2 *sv, const uint2 *s_tab, cons
 template <bool UNIF>
 __device__ __forceinline__ Fast warp_eval(const WEval &ev, const Scal &c, uint32_t wacc) {
     Fast f;
-    const float inv2 = 1.f / ev.nrm2;
-    f.inv = rsqrtf(ev.nrm2);
+    const float inv2 = rcp_rn(ev.nrm2);
+    f.inv = rsqrt_approx(ev.nrm2);
     f.S = ev.Sraw * inv2;
     f.T = ev.T * (inv2 * f.inv);
     const float tS = c.cS * f.S;
