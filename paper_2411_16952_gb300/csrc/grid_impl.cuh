@@ -185,6 +185,7 @@ struct GridWG {
     uint32_t chunk;
     uint32_t abort;
     float sig[KMAX], act[KMAX];
+    float4 md[KMAX];  // mode_consts of the point
 };
 
 // One row of a tile between its draw and its decision.
@@ -291,8 +292,10 @@ __global__ void __launch_bounds__(128 * NWG, 1)
         const unsigned long long cbase = A.idx0[p] + local;
         const PointConst *P = B.pts + p;
         if (t < KMAX) {
-            W.sig[t] = __ldg(&P->sigma[t]);
-            W.act[t] = __ldg(&P->act[t]);
+            const float sg = __ldg(&P->sigma[t]), ac = __ldg(&P->act[t]);
+            W.sig[t] = sg;
+            W.act[t] = ac;
+            W.md[t] = mode_consts<UNIF>(sg, ac, t);
         }
         const Scal sc = load_scal(P);
         wg_sync(g);
@@ -441,18 +444,16 @@ __global__ void __launch_bounds__(128 * NWG, 1)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int m = 2 * j + h;
-                            const float act = W.act[m];  // 1 for modes up to K, else 0
-                            const float s = UNIF ? act : W.sig[m];
+                            const float4 c = W.md[m];  // (s, s^2, (m+1)^2 s^2, act)
                             float rho, xm, ym, rr;
-                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, c.x, rho, xm, ym, rr);
                             wmin = min(wmin, h ? w.z : w.x);
-                            esum = fmaf(s, rr, esum);
+                            esum = fmaf(c.x, rr, esum);
                             vx[2 * jj + h] = xm;
                             vy[2 * jj + h] = ym;
-                            const float sk = (s * s) * rho;
-                            nrm2 += sk;
-                            Sraw = fmaf((float)((m + 1) * (m + 1)), sk, Sraw);
-                            zz = fmaf(act, rho, zz);  // the active modes' squared radii
+                            nrm2 = fmaf(c.y, rho, nrm2);
+                            Sraw = fmaf(c.z, rho, Sraw);
+                            zz = fmaf(c.w, rho, zz);  // the active modes' squared radii
                         }
                     }
                     uint4 hx, lx, hy, ly;

@@ -258,19 +258,40 @@ struct PairRow {
     __device__ __forceinline__ uint4 block(uint32_t j) const { return philox4x32_10(make_uint4(j, lo, hi, pid), k0, k1); }
 };
 
+// Per-mode constants of a draw, (s, s^2, (m+1)^2 s^2, act) with s = sigma_m
+// (the act flag for the uniform proposal), so that each accumulation of a
+// mode is one FMA with the squared radius.  ModeSigAct forms them from a
+// point's sigma and act arrays; ModeTab reads the same values from a table
+// (one 16-byte load per mode).
+template <bool UNIF>
+__device__ __forceinline__ float4 mode_consts(float sig, float act, int m) {
+    const float s = UNIF ? act : sig;
+    const float s2 = s * s;
+    return make_float4(s, s2, (float)((m + 1) * (m + 1)) * s2, act);
+}
+template <bool UNIF>
+struct ModeSigAct {
+    const float *sig, *act;
+    __device__ __forceinline__ float4 operator()(int m) const { return mode_consts<UNIF>(sig[m], act[m], m); }
+};
+struct ModeTab {
+    const float4 *md;
+    __device__ __forceinline__ float4 operator()(int m) const { return md[m]; }
+};
+
 // Steps 1-3 for modes 0..KMAX-1.  Modes beyond K have sigma = act = 0.
-template <int KMAX, bool UNIF, bool ACC = false, typename Row = PairRow>
-__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act, const Row &row);
+template <int KMAX, bool UNIF, bool ACC = false, typename Row = PairRow, typename Modes = ModeSigAct<UNIF>>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const Modes &modes, const Row &row);
 
 template <int KMAX, bool UNIF, bool ACC = false>
 __device__ __forceinline__ void draw_fast(Draw<KMAX> &d, const float *sig, const float *act,
                                           uint32_t idx_lo, uint32_t idx_hi, uint32_t pid,
                                           uint32_t k0, uint32_t k1) {
-    draw_fast_k<KMAX, UNIF, ACC>(d, sig, act, PairRow{idx_lo, idx_hi, pid, k0, k1});
+    draw_fast_k<KMAX, UNIF, ACC>(d, ModeSigAct<UNIF>{sig, act}, PairRow{idx_lo, idx_hi, pid, k0, k1});
 }
 
-template <int KMAX, bool UNIF, bool ACC, typename Row>
-__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, const float *act, const Row &row) {
+template <int KMAX, bool UNIF, bool ACC, typename Row, typename Modes>
+__device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const Modes &modes, const Row &row) {
     d.nrm2 = 0.f;
     d.Sraw = 0.f;
     d.zz = 0.f;
@@ -285,19 +306,18 @@ __device__ __forceinline__ void draw_fast_k(Draw<KMAX> &d, const float *sig, con
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
             if (m < KMAX) {
-                const float s = UNIF ? act[m] : sig[m];
+                const float4 c = modes(m);
                 float rho, xm, ym, rr;
-                box_muller_f32<ACC>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
+                box_muller_f32<ACC>(h ? w.z : w.x, h ? w.w : w.y, c.x, rho, xm, ym, rr);
                 d.wmin = min(d.wmin, h ? w.z : w.x);
-                const float srr = s * rr;
+                const float srr = c.x * rr;
                 d.esum += srr;
                 d.rrmax = fmaxf(d.rrmax, srr);
                 d.x[m] = xm;
                 d.y[m] = ym;
-                const float sk = (s * s) * rho;
-                d.nrm2 += sk;
-                d.Sraw = fmaf((float)((m + 1) * (m + 1)), sk, d.Sraw);
-                d.zz += s > 0.f ? rho : 0.f;  // modes above K have sigma = 0
+                d.nrm2 = fmaf(c.y, rho, d.nrm2);
+                d.Sraw = fmaf(c.z, rho, d.Sraw);
+                d.zz = fmaf(c.w, rho, d.zz);  // modes above K have act = 0
                 d.u0raw += xm;
             }
         }
@@ -590,12 +610,11 @@ __device__ __forceinline__ DrawSums acc_draw_sums(const float *sig, const float 
         for (int h = 0; h < 2; ++h) {
             const int m = 2 * j + h;
             if (m < KMAX) {
-                const float s = UNIF ? act[m] : sig[m];
+                const float4 c = mode_consts<UNIF>(sig[m], act[m], m);
                 float rho, xm, ym, rr;
-                box_muller_f32<true>(h ? w.z : w.x, h ? w.w : w.y, s, rho, xm, ym, rr);
-                const float sk = (s * s) * rho;
-                d.nrm2 += sk;
-                d.Sraw = fmaf((float)((m + 1) * (m + 1)), sk, d.Sraw);
+                box_muller_f32<true>(h ? w.z : w.x, h ? w.w : w.y, c.x, rho, xm, ym, rr);
+                d.nrm2 = fmaf(c.y, rho, d.nrm2);
+                d.Sraw = fmaf(c.z, rho, d.Sraw);
                 d.u0raw += xm;
             }
         }
@@ -650,6 +669,7 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ uint32_t s_maxd;
     __shared__ uint32_t s_chunk;
     __shared__ float s_sig[KMAX], s_act[KMAX];
+    __shared__ float4 s_md[KMAX];
     // dynamic: per thread, its accepted draw's scaled state (x | y), padded
     // (kXferStride floats apart, so that the lanes' vector stores spread over
     // the banks); absent in the SIR form
@@ -688,8 +708,10 @@ __global__ void __launch_bounds__(NT, MINB)
         const unsigned long long base = A.idx0[p] + local;
         const PointConst *P = B.pts + p;
         if (tid < KMAX) {
-            s_sig[tid] = __ldg(&P->sigma[tid]);
-            s_act[tid] = __ldg(&P->act[tid]);
+            const float sg = __ldg(&P->sigma[tid]), ac = __ldg(&P->act[tid]);
+            s_sig[tid] = sg;
+            s_act[tid] = ac;
+            s_md[tid] = mode_consts<UNIF>(sg, ac, tid);
         }
         const Scal sc = load_scal(P);
         __syncthreads();
@@ -703,7 +725,13 @@ __global__ void __launch_bounds__(NT, MINB)
             const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
             Draw<KMAX> dr;
             const PhiloxRow prow(lo, hi, sc.pid, A.rk.k);
-            draw_fast_k<KMAX, UNIF>(dr, s_sig, s_act, prow);
+            // the per-mode constants from the table, or formed from sigma and
+            // act where the table's loads spill under the hand-off variant's
+            // register budget (the same values either way)
+            if constexpr (XFER)
+                draw_fast_k<KMAX, UNIF>(dr, ModeSigAct<UNIF>{s_sig, s_act}, prow);
+            else
+                draw_fast_k<KMAX, UNIF>(dr, ModeTab{s_md}, prow);
             const uint32_t wa = prow.block((uint32_t)((sc.K + 1) / 2)).x;
             const Fast f = eval_fast<KMAX, UNIF>(dr, sc, wa);
             // a radius or accept word in the lowest bucket: FP64 pass (refined tail)
