@@ -73,13 +73,11 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (130304.0 / (8 * 4194304),
-             "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,4>, 8 x 2^22 proposals)"),
+    "grid": (None, "not captured since the kernel last changed"),
     "triad": (None, "not captured since the kernel last changed"),
 }
 # the 64-mode grid kernel: one capture of the upstream run at 2^26 proposals
-TRAFFIC_PER_PROPOSAL_K64 = (202752.0 / (1 << 26),
-                            "ncu --set full capture prof_grid_k64 (k_sample_grid<64,0,2,2>, 2^26 proposals)")
+TRAFFIC_PER_PROPOSAL_K64 = (None, "not captured since the kernel last changed")
 
 
 def alu_peak(n_sms, peaks):

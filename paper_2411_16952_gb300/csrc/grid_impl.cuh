@@ -15,7 +15,9 @@
 // terms onto N: half the multiply-adds of the plain grid contraction.
 //
 // On the tensor cores, for a tile of 128 proposals:
-//   C = Xc Bc,  S = Xs Bs,  Xc, Xs: 128 x K,  Bc, Bs: K x N/2,
+//   C = Xc Bc,  S' = Xs Bs,  Xc, Xs: 128 x K,  Bc, Bs: K x N/2,
+// with Bs holding sqrt(3) sin, so that S' = sqrt(3) S and a pair sums as
+// 2 C (C^2 + S'^2) (one packed multiply fewer per two pairs),
 // each as three BF16 products with FP32 accumulation in tensor memory:
 // X = Xh + Xl, B = Bh + Bl, XB ~ Xh Bh + Xh Bl + Xl Bh (the dropped Xl Bl
 // term is 2^-16 relative).  The A tile holds a row per proposal in the
@@ -33,7 +35,7 @@
 //      tcgen05.mma (M = 128, N = N/2, K = 16) and commits them to the
 //      warpgroup's mbarrier;
 //   3. every thread waits (bounded) on the mbarrier, reads its own TMEM lane
-//      (its proposal's C_j and S_j) and sums 2 C (C^2 + 3 S^2);
+//      (its proposal's C_j and S'_j) and sums 2 C (C^2 + S'^2);
 //   4. the decision is that of the triad form; an accepted draw's index,
 //      T and log f/(Mg) go to its warp's slab in global memory, and at the
 //      end of the chunk the warp makes the outputs of its slab 32 draws at a
@@ -267,7 +269,6 @@ __global__ void __launch_bounds__(128 * NWG, 1)
     // chunk / 4 proposals per warp)
     AcceptItem *slab = B.accs + ((size_t)(blockIdx.x * NWG + g) * 4 + (size_t)(t >> 5)) * B.acc_slab;
     const float tscale = 8.f / (3.f * (float)gridN);  // T = (4/(3N)) sum U^3/|x|^3, sum U^3 = 2 sum C (C^2 + 3 S^2)
-    const f32x2_t three = pk2(3.f, 3.f);
 
     const uint32_t total = A.chunk_prefix[A.n_points];
     const unsigned long long t0 = A.deadline_ns ? globaltimer_ns() : 0ull;
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
 #pragma unroll
                         for (int e = 0; e < n; e += 2) {
                             const f32x2_t C2 = pk2(cv[e], cv[e + 1]), S2 = pk2(sv[e], sv[e + 1]);
-                            const f32x2_t q = fma2(three, mul2(S2, S2), mul2(C2, C2));
+                            const f32x2_t q = fma2(S2, S2, mul2(C2, C2));  // C^2 + 3 S^2
                             acc[(e >> 1) & 1] = fma2(C2, q, acc[(e >> 1) & 1]);
                         }
                     };
