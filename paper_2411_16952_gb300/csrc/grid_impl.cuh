@@ -159,15 +159,22 @@ struct GridShape {
     static constexpr int A_TILE = 128 * KA * 2;           // bytes of one BF16 tile (hi or lo)
 };
 
-// Pack 8 floats into BF16 hi and lo halves (x = hi + lo + O(2^-16 x)).
+// Pack 8 floats into BF16 hi and lo halves (x = hi + lo + O(2^-16 x)); the
+// residuals x - hi (exact in FP32) of a pair by one packed subtraction.
 __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-        const float r0 = v[2 * q] - __low2float(hh), r1 = v[2 * q + 1] - __high2float(hh);
+        const uint32_t hb = *reinterpret_cast<const uint32_t *>(&hh);
+        f32x2_t rr;
+        asm("sub.rn.f32x2 %0, %1, %2;"
+            : "=l"(rr)
+            : "l"(pk2(v[2 * q], v[2 * q + 1])), "l"(pk2(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u))));
+        float r0, r1;
+        upk2(rr, r0, r1);
         const __nv_bfloat162 ll = __floats2bfloat162_rn(r0, r1);
-        h[q] = *reinterpret_cast<const uint32_t *>(&hh);
+        h[q] = hb;
         l[q] = *reinterpret_cast<const uint32_t *>(&ll);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
@@ -187,7 +194,9 @@ struct GridWG {
     uint32_t chunk;
     uint32_t abort;
     float sig[KMAX], act[KMAX];
-    float4 md[KMAX];  // mode_consts of the point
+    // mode_consts of the point by pairs of modes (2j, 2j + 1) = Philox block
+    // j: (s, s', s^2, s'^2) and ((m+1)^2 s^2, (m+2)^2 s'^2, act, act')
+    float4 mp[KMAX / 2][2];
 };
 
 // One row of a tile between its draw and its decision.
@@ -293,10 +302,14 @@ __global__ void __launch_bounds__(128 * NWG, 1)
         const unsigned long long cbase = A.idx0[p] + local;
         const PointConst *P = B.pts + p;
         if (t < KMAX) {
-            const float sg = __ldg(&P->sigma[t]), ac = __ldg(&P->act[t]);
-            W.sig[t] = sg;
-            W.act[t] = ac;
-            W.md[t] = mode_consts<UNIF>(sg, ac, t);
+            W.sig[t] = __ldg(&P->sigma[t]);
+            W.act[t] = __ldg(&P->act[t]);
+        }
+        if (t < KMAX / 2) {
+            const float4 a = mode_consts<UNIF>(__ldg(&P->sigma[2 * t]), __ldg(&P->act[2 * t]), 2 * t);
+            const float4 b = mode_consts<UNIF>(__ldg(&P->sigma[2 * t + 1]), __ldg(&P->act[2 * t + 1]), 2 * t + 1);
+            W.mp[t][0] = make_float4(a.x, b.x, a.y, b.y);
+            W.mp[t][1] = make_float4(a.z, b.z, a.w, b.w);
         }
         const Scal sc = load_scal(P);
         wg_sync(g);
@@ -432,7 +445,8 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 const uint32_t lo = (uint32_t)idx, hi = (uint32_t)(idx >> 32);
                 // ---- 1. the row of X: eight modes (four Philox blocks) at a time,
                 // cosine values to part 0 and sine values to part 1 of the row
-                float nrm2 = 0.f, Sraw = 0.f, zz = 0.f, esum = 0.f;
+                // the mode sums over even and odd modes in packed pairs
+                f32x2_t nrm2p = 0ull, Srawp = 0ull, zzp = 0ull, esump = 0ull;
                 uint32_t wmin = 0xFFFFFFFFu;
                 const PhiloxRow prow(lo, hi, sc.pid, A.rk.k);
 #pragma unroll(UNR)
@@ -442,20 +456,16 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = 4 * c8 + jj;
                         const uint4 w = prow.block((uint32_t)j);
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int m = 2 * j + h;
-                            const float4 c = W.md[m];  // (s, s^2, (m+1)^2 s^2, act)
-                            float rho, xm, ym, rr;
-                            box_muller_f32<false>(h ? w.z : w.x, h ? w.w : w.y, c.x, rho, xm, ym, rr);
-                            wmin = min(wmin, h ? w.z : w.x);
-                            esum = fmaf(c.x, rr, esum);
-                            vx[2 * jj + h] = xm;
-                            vy[2 * jj + h] = ym;
-                            nrm2 = fmaf(c.y, rho, nrm2);
-                            Sraw = fmaf(c.z, rho, Sraw);
-                            zz = fmaf(c.w, rho, zz);  // the active modes' squared radii
-                        }
+                        const float4 c0 = W.mp[j][0], c1 = W.mp[j][1];
+                        float rho0, rho1, rr0, rr1;
+                        box_muller_f32<false>(w.x, w.y, c0.x, rho0, vx[2 * jj], vy[2 * jj], rr0);
+                        box_muller_f32<false>(w.z, w.w, c0.y, rho1, vx[2 * jj + 1], vy[2 * jj + 1], rr1);
+                        wmin = min(wmin, min(w.x, w.z));
+                        const f32x2_t rho2 = pk2(rho0, rho1);
+                        esump = fma2(pk2(c0.x, c0.y), pk2(rr0, rr1), esump);
+                        nrm2p = fma2(pk2(c0.z, c0.w), rho2, nrm2p);
+                        Srawp = fma2(pk2(c1.x, c1.y), rho2, Srawp);
+                        zzp = fma2(pk2(c1.z, c1.w), rho2, zzp);  // the active modes' squared radii
                     }
                     uint4 hx, lx, hy, ly;
                     split8(vx, hx, lx);
@@ -467,12 +477,17 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                     *reinterpret_cast<uint4 *>(ga_hi + oy) = hy;
                     *reinterpret_cast<uint4 *>(ga_lo + oy) = ly;
                 }
+                float e0, e1;
                 cur.idx = idx;
                 cur.valid = i < n_here;
-                cur.nrm2 = nrm2;
-                cur.Sraw = Sraw;
-                cur.zz = zz;
-                cur.esum = esum;
+                upk2(nrm2p, e0, e1);
+                cur.nrm2 = e0 + e1;
+                upk2(Srawp, e0, e1);
+                cur.Sraw = e0 + e1;
+                upk2(zzp, e0, e1);
+                cur.zz = e0 + e1;
+                upk2(esump, e0, e1);
+                cur.esum = e0 + e1;
                 cur.tail = wmin < kTailBucket;
             }
             {  // ---- 2. after the warpgroup barrier one thread issues the contraction of the tile
