@@ -159,6 +159,35 @@ struct GridShape {
     static constexpr int A_TILE = 128 * KA * 2;           // bytes of one BF16 tile (hi or lo)
 };
 
+// The two Box-Muller pairs of one Philox block (radius words w.x, w.z, angle
+// words w.y, w.w; scales s = (s_m, s_m+1)), with the multiplications and
+// additions of the two modes as packed pairs: rho as rho_fast gives it,
+// rr = rsqrt_approx(rho), and (x, y) = s sqrt(rho) (cos, sin) of the reduced
+// angle 2 pi (u2 - 1/2).  These are the values of box_muller_f32<false> with
+// the signs of x and y flipped; the grid basis carries the same flip (its
+// values are negated), so that the products C and S' are unchanged.
+__device__ __forceinline__ void box_muller2(const uint4 w, f32x2_t s, f32x2_t &rho, f32x2_t &rr, f32x2_t &x,
+                                            f32x2_t &y) {
+    constexpr float kLn4 = 1.38629436111989061883f, k2Pi = 6.28318530717958647692f;
+    const f32x2_t f1 = pk2(__uint_as_float(0x3f800000u | (w.x >> 9)), __uint_as_float(0x3f800000u | (w.z >> 9)));
+    float u0, u1;
+    upk2(add2(f1, pk2(-0x1.fffffep-1f, -0x1.fffffep-1f)), u0, u1);  // u01f of w.x, w.z
+    float l0, l1;
+    upk2(mul2(pk2(lg2_approx(u0), lg2_approx(u1)), pk2(-kLn4, -kLn4)), l0, l1);
+    const float r0 = fmaxf(l0, 0x1p-25f), r1 = fmaxf(l1, 0x1p-25f);  // rho_fast
+    rho = pk2(r0, r1);
+    rr = pk2(rsqrt_approx(r0), rsqrt_approx(r1));
+    const f32x2_t a = mul2(mul2(s, rho), rr);
+    const f32x2_t f2 = pk2(__uint_as_float(0x3f800000u | (w.y >> 9)), __uint_as_float(0x3f800000u | (w.w >> 9)));
+    float t0, t1;  // angle_f of w.y, w.w
+    upk2(fma2(pk2(k2Pi, k2Pi), add2(f2, pk2(-1.5f, -1.5f)), pk2(k2Pi * 0x1p-24f, k2Pi * 0x1p-24f)), t0, t1);
+    float sn0, cs0, sn1, cs1;
+    sincos_approx(t0, sn0, cs0);
+    sincos_approx(t1, sn1, cs1);
+    x = mul2(a, pk2(cs0, cs1));
+    y = mul2(a, pk2(sn0, sn1));
+}
+
 // Pack 8 floats into BF16 hi and lo halves (x = hi + lo + O(2^-16 x)); the
 // residuals x - hi (exact in FP32) of a pair by one packed subtraction.
 __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
@@ -457,12 +486,13 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                         const int j = 4 * c8 + jj;
                         const uint4 w = prow.block((uint32_t)j);
                         const float4 c0 = W.mp[j][0], c1 = W.mp[j][1];
-                        float rho0, rho1, rr0, rr1;
-                        box_muller_f32<false>(w.x, w.y, c0.x, rho0, vx[2 * jj], vy[2 * jj], rr0);
-                        box_muller_f32<false>(w.z, w.w, c0.y, rho1, vx[2 * jj + 1], vy[2 * jj + 1], rr1);
+                        const f32x2_t s2 = pk2(c0.x, c0.y);
+                        f32x2_t rho2, rr2, x2, y2;
+                        box_muller2(w, s2, rho2, rr2, x2, y2);
+                        upk2(x2, vx[2 * jj], vx[2 * jj + 1]);
+                        upk2(y2, vy[2 * jj], vy[2 * jj + 1]);
                         wmin = min(wmin, min(w.x, w.z));
-                        const f32x2_t rho2 = pk2(rho0, rho1);
-                        esump = fma2(pk2(c0.x, c0.y), pk2(rr0, rr1), esump);
+                        esump = fma2(s2, rr2, esump);
                         nrm2p = fma2(pk2(c0.z, c0.w), rho2, nrm2p);
                         Srawp = fma2(pk2(c1.x, c1.y), rho2, Srawp);
                         zzp = fma2(pk2(c1.z, c1.w), rho2, zzp);  // the active modes' squared radii

@@ -344,6 +344,11 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f32x2_t add2(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // Step 4: T = sum_{n=2}^{KMAX} x_n A_n + y_n B_n, with
 //   A_n = sum_{k=1}^{n-1} x_k x_{n-k} - y_k y_{n-k},
