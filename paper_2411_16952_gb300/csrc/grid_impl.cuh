@@ -169,7 +169,7 @@ struct GridShape {
 __device__ __forceinline__ void box_muller2(const uint4 w, f32x2_t s, f32x2_t &rho, f32x2_t &rr, f32x2_t &x,
                                             f32x2_t &y) {
     constexpr float kLn4 = 1.38629436111989061883f, k2Pi = 6.28318530717958647692f;
-    const f32x2_t f1 = pk2(__uint_as_float(0x3f800000u | (w.x >> 9)), __uint_as_float(0x3f800000u | (w.z >> 9)));
+    const f32x2_t f1 = pk2(one_m(w.x), one_m(w.z));
     float u0, u1;
     upk2(add2(f1, pk2(-0x1.fffffep-1f, -0x1.fffffep-1f)), u0, u1);  // u01f of w.x, w.z
     float l0, l1;
@@ -178,7 +178,7 @@ __device__ __forceinline__ void box_muller2(const uint4 w, f32x2_t s, f32x2_t &r
     rho = pk2(r0, r1);
     rr = pk2(rsqrt_approx(r0), rsqrt_approx(r1));
     const f32x2_t a = mul2(mul2(s, rho), rr);
-    const f32x2_t f2 = pk2(__uint_as_float(0x3f800000u | (w.y >> 9)), __uint_as_float(0x3f800000u | (w.w >> 9)));
+    const f32x2_t f2 = pk2(one_m(w.y), one_m(w.w));
     float t0, t1;  // angle_f of w.y, w.w
     upk2(fma2(pk2(k2Pi, k2Pi), add2(f2, pk2(-1.5f, -1.5f)), pk2(k2Pi * 0x1p-24f, k2Pi * 0x1p-24f)), t0, t1);
     float sn0, cs0, sn1, cs1;

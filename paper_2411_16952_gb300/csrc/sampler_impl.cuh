@@ -70,12 +70,13 @@ struct PhiloxRow {
     __device__ __forceinline__ uint4 block(uint32_t j) const { return philox4x32_10_rk(make_uint4(j, lo, hi, pid), rk); }
 };
 
+// one_m(w): the float 1 + (w >> 9) 2^-23, i.e. the bits 0x3f800000 | (w >> 9),
+// by one funnel shift of (127 : w) right by 9.
+__device__ __forceinline__ float one_m(uint32_t w) { return __uint_as_float(__funnelshift_r(w, 0x7Fu, 9)); }
 // (2 floor(w/512) + 1) 2^-24, exact in FP32: the float 1 + m 2^-23 with
 // m = w >> 9 is built from its bits, and subtracting 1 - 2^-24 (a float) is
 // exact (Sterbenz), leaving (2m + 1) 2^-24.
-__device__ __forceinline__ float u01f(uint32_t w) {
-    return __uint_as_float(0x3f800000u | (w >> 9)) - 0x1.fffffep-1f;
-}
+__device__ __forceinline__ float u01f(uint32_t w) { return one_m(w) - 0x1.fffffep-1f; }
 __device__ __forceinline__ double u01d(uint32_t w) {
     return (double)((w >> 8) | 1u) * 0x1p-24;
 }
@@ -112,7 +113,7 @@ __device__ __forceinline__ double u01d_ext(uint32_t w, uint32_t g, uint32_t lo, 
 // and 2 pi (u - 1/2) = 2 pi ((1 + m 2^-23) - 3/2) + 2 pi 2^-24 takes one FMA.
 __device__ __forceinline__ float angle_f(uint32_t w) {
     constexpr float k2Pi = 6.28318530717958647692f;
-    return fmaf(k2Pi, __uint_as_float(0x3f800000u | (w >> 9)) - 1.5f, k2Pi * 0x1p-24f);
+    return fmaf(k2Pi, one_m(w) - 1.5f, k2Pi * 0x1p-24f);
 }
 
 // The hardware approximations of PTX (lg2, rsqrt, sin, cos .approx) in their
