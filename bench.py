@@ -49,20 +49,24 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
     """Ideal thread-instruction count of one proposal.
 
     Both forms: Philox4x32-10 (ceil(K/2)+1 blocks x 10 rounds x 4: two wide
-    multiplies and two 3-input xors), Box-Muller and sigma scaling (20 per
-    mode), the |x|^2, S, Q, u0 accumulations (4 per mode), 40 for log Q, ln U,
-    the ratio and the decision.
-    triad: the symmetric double sum of Eq. (42) (4 FMA per pair k < n-k, 3 for
-    the middle term, 4 for the outer update).
-    grid: BF16 hi/lo split and shared-memory store of the 2K values (3.5 per
-    value), the sum of 2 C (C^2 + 3 S^2) over the N/2 mirror pairs of grid
-    points (two packed FP32x2 instructions per two pairs and two
-    multiplications: 1 per grid point) and the TMEM loads of C and S (1 per
-    16 columns)."""
+    multiplies and two 3-input xors) and 40 for log Q, ln U, the ratio and
+    the decision.
+    triad (scalar FP32 per mode): Box-Muller and sigma scaling (20 per mode),
+    the |x|^2, S, Q, u0 accumulations (4 per mode), and the symmetric double
+    sum of Eq. (42) (4 FMA per pair k < n-k, 3 for the middle term, 4 for
+    the outer update).
+    grid (the two modes of a Philox block in packed FP32x2 pairs where the
+    data allow): per pair of modes 22 for Box-Muller and scaling (4 bit
+    shifts, 2 lg2, 2 floors, 2 rsqrt, 4 sin/cos, 8 packed multiply/add),
+    4 packed accumulations, 2 table loads and 2 minima of the radius words;
+    per value 2.5 for the BF16 hi/lo split (packed residuals) and 0.25 for
+    the 16-byte shared-memory stores; 1.5 per mirror pair of grid points
+    for 2 C (C^2 + S'^2) (three packed instructions per two pairs); one
+    TMEM load per 16 columns of C and of S.  20.5 per mode in all."""
     blocks = (K + 1) // 2 + 1
-    common = 40 * blocks + 20 * K + 4 * K + 40
     if form == "grid":
-        return int(common + 3.5 * 2 * K + grid_N + grid_N // 16)
+        return int(40 * blocks + 20.5 * K + 0.75 * grid_N + grid_N // 16 + 40)
+    common = 40 * blocks + 20 * K + 4 * K + 40
     triad = sum(4 * ((n - 1) // 2) + (3 if n % 2 == 0 else 0) + 4 for n in range(2, K + 1))
     return common + triad
 
