@@ -53,8 +53,9 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
     the decision.
     triad (scalar FP32 per mode): Box-Muller and sigma scaling (20 per mode),
     the |x|^2, S, Q, u0 accumulations (4 per mode), and the symmetric double
-    sum of Eq. (42) (4 FMA per pair k < n-k, 3 for the middle term, 4 for
-    the outer update).
+    sum of Eq. (42) in packed FP32x2 pairs (2 per pair k < n-k, 4 for the
+    middle term of an even n and 2 for the doubling of an odd one, 4 for the
+    outer update); the same count serves the warp form (K > 64).
     grid (the two modes of a Philox block in packed FP32x2 pairs where the
     data allow): per pair of modes 22 for Box-Muller and scaling (4 bit
     shifts, 2 lg2, 2 floors, 2 rsqrt, 4 sin/cos, 8 packed multiply/add),
@@ -67,7 +68,7 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
     if form == "grid":
         return int(40 * blocks + 20.5 * K + 0.75 * grid_N + grid_N // 16 + 40)
     common = 40 * blocks + 20 * K + 4 * K + 40
-    triad = sum(4 * ((n - 1) // 2) + (3 if n % 2 == 0 else 0) + 4 for n in range(2, K + 1))
+    triad = sum(2 * ((n - 1) // 2) + (4 if n % 2 == 0 else 2) + 4 for n in range(2, K + 1))
     return common + triad
 
 
@@ -77,11 +78,14 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": (None, "not captured since the kernel last changed"),
-    "triad": (None, "not captured since the kernel last changed"),
+    "grid": ((128256.0 + 256.0) / (8 * 4194304),
+             "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,4>, 8 x 2^22 proposals)"),
+    "triad": (116736.0 / (8 * 4194304),
+              "ncu --set full capture prof_triad (k_sample_triad<32,0,256,1,0,1>, 8 x 2^22 proposals)"),
 }
 # the 64-mode grid kernel: one capture of the upstream run at 2^26 proposals
-TRAFFIC_PER_PROPOSAL_K64 = (None, "not captured since the kernel last changed")
+TRAFFIC_PER_PROPOSAL_K64 = (215040.0 / (1 << 26),
+                            "ncu --set full capture prof_grid_k64 (k_sample_grid<64,0,2,2>, 2^26 proposals)")
 
 
 def alu_peak(n_sms, peaks):

@@ -29,8 +29,10 @@
 // and shared; every warpgroup owns one A tile (hi and lo), one pair of TMEM
 // accumulators (C and S, N/2 columns each) and one mbarrier, and runs its own
 // persistent loop over chunks of proposal indices:
-//   1. each thread makes its proposal (Philox, Box-Muller, sigma scaling as in
-//      the triad form) and writes its row of Xh and Xl;
+//   1. each thread makes its proposal (Philox, Box-Muller, sigma scaling: the
+//      values of the triad form with the signs of the components flipped,
+//      the two modes of a Philox block in packed FP32 pairs) and writes its
+//      row of Xh and Xl (the basis is negated to match);
 //   2. after a warpgroup barrier one thread issues the 2 x 3 x K/16
 //      tcgen05.mma (M = 128, N = N/2, K = 16) and commits them to the
 //      warpgroup's mbarrier;
