@@ -564,6 +564,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
             unsigned long long slot0 = 0;
             if (lane == 0) slot0 = atomicAdd(B.ring_count, (unsigned long long)__popc(mh));
             slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            unsigned long long qv[4] = {0ull, 0ull, 0ull, 0ull};  // u0 power sums, summed over the warp first
             if (has) {
                 const AcceptItem it = slab[b0 + lane];
                 const uint32_t ilo = (uint32_t)it.idx, ihi = (uint32_t)(it.idx >> 32);
@@ -574,10 +575,10 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                 atomicAdd(&W.hist[hist_bin(u0, sc.ha, sc.hb)], 1u);
                 atomicAdd(&W.exc[exc_bin(u0, sc.ea)], 1u);
                 const float u2 = u0 * u0;
-                atomicAdd(&W.q[0], (unsigned long long)__float2ll_rn(u0 * kQ1));
-                atomicAdd(&W.q[1], (unsigned long long)__float2ll_rn(u2 * kQ2));
-                atomicAdd(&W.q[2], (unsigned long long)__float2ll_rn(u2 * u0 * kQ3));
-                atomicAdd(&W.q[3], (unsigned long long)__float2ll_rn(u2 * u2 * kQ4));
+                qv[0] = (unsigned long long)__float2ll_rn(u0 * kQ1);
+                qv[1] = (unsigned long long)__float2ll_rn(u2 * kQ2);
+                qv[2] = (unsigned long long)__float2ll_rn(u2 * u0 * kQ3);
+                qv[3] = (unsigned long long)__float2ll_rn(u2 * u2 * kQ4);
                 const unsigned long long slot = slot0 + __popc(mh & ((1u << lane) - 1u));
                 unsigned char *rec = nullptr;
                 if (slot < B.ring_cap) {
@@ -587,7 +588,15 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                     atomicAdd(&W.cnt[2], 1u);
                 }
                 acc_draw_emit<KMAX, UNIF>(W.sig, W.act, ilo, ihi, sc.pid, k0, k1, inv, inv2, sc.K,
-                                          rec ? reinterpret_cast<float *>(rec + 32) : nullptr, W.spec);
+                                          rec ? reinterpret_cast<float *>(rec + 32) : nullptr, W.spec,
+                                          lane % ((KMAX + 1) / 2));
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {  // fixed-point sums: exact in any order
+                unsigned long long v = qv[e];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && v) atomicAdd(&W.q[e], v);
             }
         }
 

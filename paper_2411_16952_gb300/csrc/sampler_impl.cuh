@@ -630,10 +630,14 @@ __device__ __forceinline__ DrawSums acc_draw_sums(const float *sig, const float 
 template <int KMAX, bool UNIF>
 __device__ __forceinline__ void acc_draw_emit(const float *sig, const float *act, uint32_t lo, uint32_t hi,
                                               uint32_t pid, uint32_t k0, uint32_t k1, float inv, float inv2, int K,
-                                              float *xh, unsigned long long *s_spec) {
+                                              float *xh, unsigned long long *s_spec, int rot = 0) {
+    // rot: the block this lane starts at, so that the lanes of a warp tally
+    // different modes at a time (the integer sums do not depend on the order)
+    constexpr int NB = (KMAX + 1) / 2;
     const float sc = inv2 * kSpecScale;
 #pragma unroll 1
-    for (int j = 0; j < (KMAX + 1) / 2; ++j) {
+    for (int jr = 0; jr < NB; ++jr) {
+        const int j = jr + rot < NB ? jr + rot : jr + rot - NB;
         const uint4 w = philox4x32_10(make_uint4((uint32_t)j, lo, hi, pid), k0, k1);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
