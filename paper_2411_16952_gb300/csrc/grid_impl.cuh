@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                     pending = false;
                     tc_fence_after();
                     // 32 columns of C and of S per wait where registers allow
-                    // (fewer round trips), then 16 at a time
+                    // (fewer round trips), then 16 at a time (16 only at 64
+                    // modes, where the 32-column loads spill: 5.81e9 against
+                    // 5.57e9 proposals/s)
                     f32x2_t acc[2] = {0ull, 0ull};
                     auto cube_sum = [&](const float *cv, const float *sv, int n) {
 #pragma unroll
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                         }
                     };
                     int cb = 0;
-                    if (NWG <= 3) {
+                    if (NWG <= 3 && KMAX < 64) {
                         for (; cb + 32 <= half; cb += 32) {
                             float cv[32], sv[32];
                             tmem_ld16(tmem_c + lane_off + (uint32_t)cb, cv);
