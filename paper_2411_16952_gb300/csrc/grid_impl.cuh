@@ -372,10 +372,10 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                     phase ^= 1u;
                     pending = false;
                     tc_fence_after();
-                    // 32 columns of C and of S per wait where registers allow
-                    // (fewer round trips), then 16 at a time (16 only at 64
-                    // modes, where the 32-column loads spill: 5.81e9 against
-                    // 5.57e9 proposals/s)
+                    // 16 columns of C and of S per wait (32 per wait spilled
+                    // and measured slower at every launch shape: 5.57e9 against
+                    // 5.81e9 proposals/s at 64 modes, 12.04e9 against 12.17e9
+                    // with three warpgroups at 32)
                     f32x2_t acc[2] = {0ull, 0ull};
                     auto cube_sum = [&](const float *cv, const float *sv, int n) {
 #pragma unroll
@@ -386,17 +386,6 @@ __global__ void __launch_bounds__(128 * NWG, 1)
                         }
                     };
                     int cb = 0;
-                    if (NWG <= 3 && KMAX < 64) {
-                        for (; cb + 32 <= half; cb += 32) {
-                            float cv[32], sv[32];
-                            tmem_ld16(tmem_c + lane_off + (uint32_t)cb, cv);
-                            tmem_ld16(tmem_c + lane_off + (uint32_t)(cb + 16), cv + 16);
-                            tmem_ld16(tmem_s + lane_off + (uint32_t)cb, sv);
-                            tmem_ld16(tmem_s + lane_off + (uint32_t)(cb + 16), sv + 16);
-                            tmem_wait_ld();
-                            cube_sum(cv, sv, 32);
-                        }
-                    }
                     for (; cb < half; cb += 16) {
                         float cv[16], sv[16];
                         tmem_ld16(tmem_c + lane_off + (uint32_t)cb, cv);
