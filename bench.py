@@ -78,13 +78,13 @@ def alg_ops_per_proposal(K: int, form: str = "triad", grid_N: int = 128) -> int:
 # read no per-proposal input, so traffic scales with the proposals processed.
 # Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_PER_PROPOSAL = {
-    "grid": ((128256.0 + 256.0) / (8 * 4194304),
+    "grid": (137984.0 / (8 * 4194304),
              "ncu --set full capture prof_grid_k32 (k_sample_grid<32,0,4,4>, 8 x 2^22 proposals)"),
     "triad": (116736.0 / (8 * 4194304),
               "ncu --set full capture prof_triad (k_sample_triad<32,0,256,1,0,1>, 8 x 2^22 proposals)"),
 }
 # the 64-mode grid kernel: one capture of the upstream run at 2^26 proposals
-TRAFFIC_PER_PROPOSAL_K64 = (215040.0 / (1 << 26),
+TRAFFIC_PER_PROPOSAL_K64 = (184576.0 / (1 << 26),
                             "ncu --set full capture prof_grid_k64 (k_sample_grid<64,0,2,2>, 2^26 proposals)")
 
 
